@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 TENO-AA SSP-RK3 steps on the 3D 256^3 periodic workload.
+
+One step = the per-problem CFL reduction (teno_cfl_dt) followed by one SSP-RK3
+step (teno_rk3_step, three right-hand-side evaluations with x/y/z face sweeps
+and the stage combinations), all on the device, dt kept on the device.
+value = cell-updates/s over all ranks (each rank advances its own independent
+256^3 problem: weak scaling, no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme 8|10]
+  python bench.py --impl reference      # the CPU oracle on the host cores
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FP64 TENO-AA cell-updates/s, 3D 256^3"
+UNIT = "cell-updates/s"
+N_SM = 152
+FP64_FLOP_PER_CLK_SM = 4          # 2 DFMA lanes per SM per clock (1.25 TFLOP/s at 2.07 GHz)
+SM_MAX_MHZ = 2070.0
+HBM_BYTES_PER_CELL_UPDATE_3D = 320.0   # 3 fused stages: 80 + 120 + 120 B (ncons = 5)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", type=int, default=10, choices=[8, 10])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FP64 work (add/sub/mul/div/sqrt = 1 flop, fma = 2 flops),
+# counted from the operations the method prescribes per face and per cell
+# ---------------------------------------------------------------------------
+
+def flops_per_cell_sweep(nd):
+    # primitive variables, sound speed, enthalpy, sqrt(rho), physical flux
+    # (4 nd + 11) and the three characteristic speeds |u-c|, |u+c|, |u|+c
+    return 4 * nd + 11 + 3
+
+
+def flops_face_fixed(nd, H):
+    nc = nd + 2
+    roe = 6 * nd + 17
+    eig = 3 * nd + 14
+    proj = nc * 2 * H * 2 * (2 * nc - 1)
+    split = nc * 2 * H * 6
+    back = nc * (2 * nc - 1) + nc
+    return roe + eig + proj + split + back
+
+
+def beta_large_flops(w):
+    k = w - 1                          # non-zero shifted values
+    return k + k * k + 2 * k - 1
+
+
+def recon_flops(H, flag):
+    """Algorithmic flops of one reconstruction given its decision byte."""
+    base = 48 + 33 + 18 + 2            # C_T measure, small indicators, their gammas, sum
+    sel = flag & 3
+    tested = []
+    for L in range(H, 2, -1):
+        tested.append(L)
+        if sel == L - 2:
+            break
+    f = base
+    for L in tested:
+        f += beta_large_flops(2 * L) + 8
+    if sel:
+        f += 2 * (2 * sel + 4) - 1     # linear scheme of S_(sel+2), width 2(sel+2)
+    else:
+        f += 29
+    return f
+
+
+def flops_per_face_from_flags(flags_np, nd, H):
+    import numpy as np
+    hist = np.bincount(flags_np & 3, minlength=4).astype(np.float64)
+    nrec = flags_np.size
+    per = {s: recon_flops(H, s) for s in range(4)}
+    tot_rec = sum(hist[s] * per[s] for s in range(4))
+    nfaces = nrec / ((nd + 2) * 2)
+    return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + tot_rec / nfaces, hist / nrec
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(device_index)], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4)
+                          if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(U, n, scheme, target_s, threads):
+    """One SSP-RK3 step of the oracle on a periodic z-slab n x n x nz of the
+    same field (identical per-cell work); nz chosen for ~target_s seconds."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    U5 = U.reshape(5, n, n, n)
+    H = scheme // 2
+
+    def slab(nz):
+        Us = np.ascontiguousarray(U5[:, :nz]).reshape(5, -1)
+        p = oracle.params(3, [n, n, nz], [2 * np.pi / n] * 3, scheme=scheme, bc=0)
+        return p, Us
+
+    p, Us = slab(H)
+    t0 = time.perf_counter()
+    oracle.rhs(p, Us, threads=threads)
+    t_rhs = time.perf_counter() - t0
+    per_cell_step = 3.0 * t_rhs / (n * n * H)
+    nz = int(max(H, min(n, target_s / max(per_cell_step * n * n, 1e-9))))
+    p, Us = slab(nz)
+    dt, _, _ = oracle.cfl_dt(p, Us, 0.4)
+    t0 = time.perf_counter()
+    oracle.rk3_step(p, Us, dt, threads=threads)
+    t = time.perf_counter() - t0
+    cells = n * n * nz
+    return cells / t, "1 SSP-RK3 step of TENO%d-AA on a periodic %dx%dx%d z-slab of the same " \
+        "field (%d cells), %d OpenMP threads" % (scheme, n, n, nz, cells, threads), nz
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import workloads
+    oracle.build()
+    n, scheme = args.n, args.scheme
+    case = workloads.tgv_3d(n, scheme=scheme)
+    threads = host_cores()
+    H = scheme // 2
+    nz = max(H, 8)
+    U5 = case["U"].reshape(5, n, n, n)
+    Us = np.ascontiguousarray(U5[:, :nz]).reshape(5, -1)
+    p = oracle.params(3, [n, n, nz], [2 * np.pi / n] * 3, scheme=scheme, bc=0)
+    for _ in range(args.warmup):
+        dt, _, _ = oracle.cfl_dt(p, Us, 0.4)
+        Us, _ = oracle.rk3_step(p, Us, dt, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt, _, _ = oracle.cfl_dt(p, Us, 0.4)
+        Us, _ = oracle.rk3_step(p, Us, dt, threads=threads)
+    t = time.perf_counter() - t0
+    cells = n * n * nz
+    value = cells * args.steps / t
+    sample = ("per step: CFL dt + 1 SSP-RK3 step of TENO%d-AA on a periodic %dx%dx%d z-slab "
+              "of the 256^3 field, %d OpenMP threads" % (scheme, n, n, nz, threads))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "3D Euler 256^3 periodic, Taylor-Green Mach 0.5 + k^-5/3 "
+                                   "solenoidal field, TENO%d-AA, LLF, CFL 0.4" % scheme,
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def read_traffic_per_face(scheme):
+    """Measured DRAM bytes per face of the face sweep, from the committed ncu
+    summary (a line 'traffic_bytes_per_face[TENO<s>]: <value>')."""
+    path = os.path.join(ROOT, "profiles", "face_sweep_3d.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"traffic_bytes_per_face\[TENO%d\]:\s*([0-9.eE+-]+)" % scheme, open(path).read())
+    return float(m.group(1)) if m else None
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2109_14340_gb300 as T
+    import workloads
+    from paper_2109_14340_gb300 import _build
+    _build.build()
+    T.load()
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, scheme = args.n, args.scheme
+    case = workloads.tgv_3d(n, seed=3001 + rank, scheme=scheme)
+    p = T.teno_params_init(ndim=3, n=[n, n, n], dx=case["dx"], scheme=scheme,
+                           bc_lo=[0, 0, 0], bc_hi=[0, 0, 0])
+    solver = T.Solver(p, dev)
+    U = torch.from_numpy(case["U"]).to(dev)
+    U0 = U.clone()
+    cells = n ** 3
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        solver.cfl_dt(U)
+        solver.step(U)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # decision histogram of the current state (untimed) -> algorithmic flops
+    _, flags = solver.rhs(U, flags=True)
+    fl_np = flags.cpu().numpy()
+    fpf, hist = flops_per_face_from_flags(fl_np, 3, scheme // 2)
+    del flags, fl_np
+
+    clocks = ClockSampler(local_rank)
+    T.teno_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    face_ms, face_launches, face_faces = T.teno_profile_read()
+    T.teno_profile_enable(False)
+    clk = clocks.stop()
+    nonphys = solver.status()
+
+    t_max = ms
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * cells * args.steps / (t_max * 1e-3)
+
+    # e2e: host buffers through teno_advance_host, one step per call
+    # (H2D of the state, CFL + RK3 step, D2H of the state, every step)
+    Uh = U0.cpu().pin_memory()
+    Ud2 = torch.empty_like(U0)
+    ws2 = torch.zeros_like(solver.ws)
+    T.teno_advance_host(p, Uh, Ud2, 1, 0.4, ws2)         # warm
+    k_e2e = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        T.teno_advance_host(p, Uh, Ud2, 1, 0.4, ws2)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = world * cells * k_e2e / t_e2e
+    state_bytes = 5 * cells * 8
+
+    # FP64 probe (context): measured DFMA rate on this GPU
+    probe = None
+    try:
+        import ctypes
+        plib = ctypes.CDLL(_build.build_probe())
+        plib.teno_probe_dfma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]
+        blocks = N_SM * 8
+        sink = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+        pms = ctypes.c_double()
+        ptot = ctypes.c_int64()
+        rc = plib.teno_probe_dfma(blocks, 20000, ctypes.c_void_p(sink.data_ptr()),
+                                  ctypes.byref(pms), ctypes.byref(ptot),
+                                  ctypes.c_void_p(stream.cuda_stream))
+        if rc == 0:
+            probe = 2.0 * ptot.value / (pms.value * 1e-3) / 1e12
+    except Exception:
+        probe = None
+
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    avg_launch_s = face_ms * 1e-3 / max(face_launches, 1)
+    faces_per_launch = face_faces / max(face_launches, 1)
+    achieved = fpf * faces_per_launch / avg_launch_s / 1e12
+    traffic_pf = read_traffic_per_face(scheme)
+    launches_per_step = 2 + 3 * (2 + 3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        threads = host_cores()
+        rate, sample, _ = oracle_sample_rate(case["U"], n, scheme, args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {
+            "workload": "3D Euler 256^3 periodic on [0,2pi]^3, Taylor-Green Mach 0.5 + seeded "
+                        "k^-5/3 solenoidal field (10% rms), TENO%d-AA, LLF, CFL 0.4; step = "
+                        "device CFL reduction + SSP-RK3 step" % scheme,
+            "scheme": scheme, "cells": cells, "parallelism": "independent problem per GPU",
+            "l2": "state 671 MB > 129 MB L2 (no flush needed)"},
+        "roofline": {
+            "bound": "alu", "kernel": "face_kernel (x/y/z face sweeps)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "peak_probe_measured": probe,
+            "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
+            "algorithmic_flops_per_face": fpf, "faces_per_launch": faces_per_launch,
+            "avg_launch_ms": avg_launch_s * 1e3,
+            "face_kernel_share": face_ms / ms if ms > 0 else None,
+            "selection_mix": {"fallback": hist[0], "S3": hist[1], "S4": hist[2], "S5": hist[3]}},
+        "roofline_hbm": {
+            "bound": "hbm", "achieved": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9,
+            "peak": 6782.1, "unit": "GB/s",
+            "frac": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9 / 6782.1,
+            "note": "algorithmic 320 B per cell-update; the path is FP64-ALU bound"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes + 8,
+                "call": "teno_advance_host(nsteps=1) from pinned host memory"},
+        "gpu_launches": launches_per_step * args.steps,
+        "nonphysical": nonphys,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * teno.h -- C ABI of the GB300 (sm_103a) TENO-AA compressible-Euler library.
+ *
+ * The library evaluates the semi-discrete right-hand side of the compressible
+ * Euler equations (arXiv 2109.14340, Sec. 1 Eq. Euler; Sec. 2 Eq.
+ * approximateEq) with the eight- or ten-point TENO-AA reconstruction (Sec. 3,
+ * Sec. 4) of Roe-averaged characteristic, flux-split fluxes (Sec. 5), and
+ * advances it with SSP-RK3 (Sec. 5, Eq. Runge-kutta) under a CFL time step.
+ *
+ * Conventions shared by every call:
+ *  - State arrays are FP64, structure of arrays, interior cells only:
+ *    U[c * ncells + (x + n[0] * (y + n[1] * z))], c = 0 .. ncons-1 with
+ *    ncons = ndim + 2 and order (rho, rho*u_x, [rho*u_y, [rho*u_z,]] E).
+ *    They live in device memory owned by the caller, 16-byte aligned.
+ *  - Every call is enqueued on the caller's stream (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).  No call allocates memory or
+ *    synchronises, except teno_status (which synchronises the stream) and
+ *    teno_advance_host (which copies host buffers and synchronises).
+ *  - The workspace ws (ws_bytes >= teno_workspace_bytes) is device memory
+ *    owned by the caller; calls sharing one workspace must be ordered on one
+ *    stream.  Its contents carry no state between calls except the
+ *    non-physical counter read by teno_status.
+ *  - Every call returns TENO_OK or an error code; parameters are validated
+ *    on the host before anything is enqueued.  Physical validity of the state
+ *    (rho > 0, p > 0, finite values, positive Roe sound speed squared) is
+ *    checked on the device without trapping: offending cells and faces are
+ *    counted and reported by teno_status.
+ */
+#ifndef TENO_H
+#define TENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define TENO_OK 0
+#define TENO_EINVAL 1          /* bad parameter, pointer, size or alignment   */
+#define TENO_ECUDA 2           /* a CUDA runtime call failed                  */
+#define TENO_ENONPHYSICAL 3    /* teno_status: non-physical states were seen  */
+#define TENO_ETIMEOUT 4        /* a bounded device-side wait gave up          */
+
+/* Boundary conditions per axis side (App. A). */
+#define TENO_BC_PERIODIC 0     /* App. A.4: ghost -r = cell n-r (both sides)  */
+#define TENO_BC_TRANSMISSIVE 1 /* zero-order extrapolation: ghost = end cell  */
+#define TENO_BC_SLIPWALL 2     /* App. A.1: ghost -r = cell r-1, normal
+                                  momentum negated                            */
+
+/* Flux splitting of the characteristic fluxes (Sec. 5). */
+#define TENO_SPLIT_LLF 0       /* per field k: alpha_k = max |lambda_k| over
+                                  the stencil cells                           */
+#define TENO_SPLIT_RUSANOV 1   /* all fields: alpha = max (|u_d| + c) over the
+                                  stencil cells                               */
+
+typedef struct teno_params {
+    int32_t ndim;          /* 1, 2 or 3                                         */
+    int32_t scheme;        /* 8 (TENO8-AA, Sec. 4.3) or 10 (TENO10-AA, Sec. 4.2) */
+    int32_t flux_split;    /* TENO_SPLIT_LLF or TENO_SPLIT_RUSANOV              */
+    int32_t limiter;       /* 1: positivity-preserving flux limiter (Sec. 5.3)  */
+    int64_t n[3];          /* interior cells per axis, x fastest; 1 if unused   */
+    double dx[3];          /* uniform spacing per axis (> 0)                    */
+    double gamma;          /* ratio of specific heats (> 1), ideal-gas EOS      */
+    double ct_alpha1;      /* alpha_1 of Eq. CT_definition, default 14          */
+    double ct_alpha2;      /* alpha_2 of Eq. CT_definition, default 6.4         */
+    double ct_cr;          /* C_r of Eq. m_definition, default 0.265            */
+    double eps_beta;       /* epsilon of Eq. scale_separation, default 1e-40    */
+    double eps_eta;        /* epsilon of the eta measure (Sec. 3.4), 1e-40      */
+    double limiter_eps;    /* density / pressure floor of the limiter, 1e-13    */
+    int32_t q;             /* exponent of Eq. scale_separation; must be 7       */
+    int32_t bc_lo[3];      /* TENO_BC_* at the low end of each axis             */
+    int32_t bc_hi[3];      /* TENO_BC_* at the high end of each axis            */
+    int32_t reserved;      /* must be 0                                          */
+} teno_params;
+
+/* Fill *p with the paper's built-in parameters (eps = 1e-40, q = 7 of Sec.
+ * 3.2; C_r = 0.265, alpha_1 = 14, alpha_2 = 6.4 of Sec. 3.4), gamma = 1.4,
+ * TENO8-AA, LLF, no limiter, periodic 1D grid of one cell (caller sets n, dx). */
+void teno_params_init(teno_params *p);
+
+/* Workspace bytes needed by every call below for these parameters.
+ * Returns TENO_EINVAL for invalid parameters (then *bytes is untouched). */
+int teno_workspace_bytes(const teno_params *p, size_t *bytes);
+
+/* Bytes of the per-face decision record written by teno_rhs (flags != NULL):
+ * for each direction d < ndim, for each face of the face grid (n with
+ * n[d] + 1, x fastest), for each characteristic field k < ncons, for the
+ * + then - split flux, one byte: bits 0-1 selected large stencil S_L as
+ * L - 2 (1: S3, 2: S4, 3: S5) or 0 for the small-stencil fallback of Eq.
+ * renormalize; bits 2-4 the cut-offs delta_0..delta_2 of Eq. cutoff in the
+ * fallback (else 0); bits 5-7 the C_T exponent [beta] of Eq. CT_definition
+ * minus 7 (mod 8). */
+int teno_flags_bytes(const teno_params *p, size_t *bytes);
+
+/* Semi-discrete right-hand side L(U) = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d
+ * (Eq. approximateEq, dimension by dimension as in Sec. 5).
+ *   U          device, ncons * ncells doubles (read)
+ *   rhs        device, ncons * ncells doubles (written); must not alias U
+ *   dt_limiter time step used by the limiter's one-sided updates (ignored
+ *              when p->limiter == 0)
+ *   flags      device, teno_flags_bytes bytes, or NULL
+ *   ws         device workspace of ws_bytes bytes */
+int teno_rhs(const teno_params *p, const double *U, double *rhs, double dt_limiter,
+             uint8_t *flags, void *ws, size_t ws_bytes, void *stream);
+
+/* One SSP-RK3 step (Eq. Runge-kutta) in place on U:
+ *   U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ *   U  <- 1/3 U + 2/3 (U2 + dt L(U2)).
+ * dt is read from dt_device (device scalar) when it is not NULL, else the
+ * host value dt is used.  Each stage's limiter uses the same dt. */
+int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_device,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* CFL time step (Sec. 5, CFL number 0.4 by default):
+ *   A_d = max over cells of (|u_d| + c), dt = cfl / sum_d (A_d / dx_d),
+ * written to the device scalar *dt_device (and kept in the workspace). */
+int teno_cfl_dt(const teno_params *p, const double *U, double cfl, double *dt_device,
+                void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronise the stream, read and clear the workspace's non-physical
+ * counter (cells with rho <= 0, p <= 0 or non-finite values in a state whose
+ * RHS was evaluated, plus faces with a non-positive Roe sound speed squared).
+ * Returns TENO_ENONPHYSICAL if the count was non-zero, else TENO_OK. */
+int teno_status(void *ws, void *stream, int64_t *nonphysical);
+
+/* End-to-end call on HOST memory: copy U_host (ncons * ncells doubles) to the
+ * device buffer U_dev, advance nsteps SSP-RK3 steps, each with dt from
+ * teno_cfl_dt(cfl) computed on the device, copy the state back to U_host and
+ * the summed time to *t_host, then synchronise the stream. */
+int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int nsteps,
+                      double cfl, double *t_host, void *ws, size_t ws_bytes, void *stream);
+
+/* Live timing of the dominant kernel (the face-sweep kernel) for roofline
+ * reporting.  teno_profile_enable(1) clears the record and from then on
+ * brackets every face-sweep launch with a pair of CUDA events recorded on
+ * the launch's stream (at most 8192 launches are recorded); (0) stops.
+ * teno_profile_read synchronises the recorded events and returns the summed
+ * device milliseconds, the number of launches and the number of faces they
+ * computed.  Not safe to call concurrently from several host threads.  The
+ * paper has no counterpart: this is measurement support. */
+int teno_profile_enable(int on);
+int teno_profile_read(double *ms, int64_t *launches, int64_t *faces);
+
+/* Human-readable text of a return code (static storage). */
+const char *teno_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TENO_H */

@@ -670,7 +670,7 @@ static void wave_maxima(const or_params *P, const double *U, double *A, int64_t 
         if (nonphysical_cell(&q)) nbad++;
         for (int a = 0; a < nd; a++) {
             double e = fabs(q.u[a]) + q.c;
-            if (id == 0 || e > Am[a]) Am[a] = e;
+            if (e > Am[a]) Am[a] = e;            /* NaN never enters the max */
         }
     }
     for (int a = 0; a < 3; a++) A[a] = Am[a];

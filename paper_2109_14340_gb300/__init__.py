@@ -1,0 +1,243 @@
+"""Python binding of the GB300 TENO-AA library (C ABI in include/teno.h).
+
+Argument marshalling only: every step of the right-hand side, the RK3 step and
+the CFL reduction runs in the sm_103a kernels of libteno_gb300.so.  PyTorch
+supplies device memory (CUDA tensors) and streams.  There is no CPU fallback:
+if the shared library is missing the calls raise.
+
+The function names mirror the C entry points:
+  teno_params_init, teno_workspace_bytes, teno_flags_bytes, teno_rhs,
+  teno_rk3_step, teno_cfl_dt, teno_status, teno_advance_host, teno_strerror.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+TENO_OK, TENO_EINVAL, TENO_ECUDA, TENO_ENONPHYSICAL, TENO_ETIMEOUT = 0, 1, 2, 3, 4
+TENO_BC_PERIODIC, TENO_BC_TRANSMISSIVE, TENO_BC_SLIPWALL = 0, 1, 2
+TENO_SPLIT_LLF, TENO_SPLIT_RUSANOV = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TenoError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (code %d)" % (what, teno_strerror(code), code))
+        self.code = code
+
+
+class teno_params(ctypes.Structure):
+    """Mirror of struct teno_params (include/teno.h)."""
+    _fields_ = [
+        ("ndim", ctypes.c_int32), ("scheme", ctypes.c_int32),
+        ("flux_split", ctypes.c_int32), ("limiter", ctypes.c_int32),
+        ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double), ("ct_alpha1", ctypes.c_double),
+        ("ct_alpha2", ctypes.c_double), ("ct_cr", ctypes.c_double),
+        ("eps_beta", ctypes.c_double), ("eps_eta", ctypes.c_double),
+        ("limiter_eps", ctypes.c_double), ("q", ctypes.c_int32),
+        ("bc_lo", ctypes.c_int32 * 3), ("bc_hi", ctypes.c_int32 * 3),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libteno_gb300.so (build it first with build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libteno_gb300.so is not built (run __graft_entry__.build() or "
+                               "paper_2109_14340_gb300._build.build()); there is no fallback")
+        lib = ctypes.CDLL(_build.LIB)
+        P = ctypes.POINTER(teno_params)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        lib.teno_params_init.argtypes = [P]
+        lib.teno_params_init.restype = None
+        lib.teno_workspace_bytes.argtypes = [P, ctypes.POINTER(sz)]
+        lib.teno_flags_bytes.argtypes = [P, ctypes.POINTER(sz)]
+        lib.teno_rhs.argtypes = [P, vp, vp, ctypes.c_double, vp, vp, sz, vp]
+        lib.teno_rk3_step.argtypes = [P, vp, ctypes.c_double, vp, vp, sz, vp]
+        lib.teno_cfl_dt.argtypes = [P, vp, ctypes.c_double, vp, vp, sz, vp]
+        lib.teno_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.teno_advance_host.argtypes = [P, vp, vp, ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double), vp, sz, vp]
+        lib.teno_profile_enable.argtypes = [ctypes.c_int]
+        lib.teno_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]
+        lib.teno_strerror.argtypes = [ctypes.c_int]
+        lib.teno_strerror.restype = ctypes.c_char_p
+        for name in ("teno_workspace_bytes", "teno_flags_bytes", "teno_rhs", "teno_rk3_step",
+                     "teno_cfl_dt", "teno_status", "teno_advance_host", "teno_profile_enable",
+                     "teno_profile_read"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno_rhs",
+           "teno_rk3_step", "teno_cfl_dt", "teno_status", "teno_advance_host",
+           "teno_profile_enable", "teno_profile_read", "teno_strerror")
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+def _check(code, what):
+    if code != TENO_OK:
+        raise TenoError(code, what)
+
+
+def teno_strerror(code: int) -> str:
+    return load().teno_strerror(int(code)).decode()
+
+
+def teno_params_init(**kw) -> teno_params:
+    """Paper defaults (Sec. 3.2, 3.4), then keyword overrides.  Sequences for
+    n, dx, bc_lo, bc_hi are padded to three axes (n: 1, dx: 1.0, bc: 0)."""
+    p = teno_params()
+    load().teno_params_init(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("n", "dx", "bc_lo", "bc_hi"):
+            v = list(v)
+            pad = {"n": 1, "dx": 1.0, "bc_lo": 0, "bc_hi": 0}[k]
+            v = v + [pad] * (3 - len(v))
+            arr = getattr(p, k)
+            for i in range(3):
+                arr[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def teno_workspace_bytes(p: teno_params) -> int:
+    n = ctypes.c_size_t()
+    _check(load().teno_workspace_bytes(ctypes.byref(p), ctypes.byref(n)), "teno_workspace_bytes")
+    return n.value
+
+
+def teno_flags_bytes(p: teno_params) -> int:
+    n = ctypes.c_size_t()
+    _check(load().teno_flags_bytes(ctypes.byref(p), ctypes.byref(n)), "teno_flags_bytes")
+    return n.value
+
+
+def teno_rhs(p, U, rhs, dt_limiter=0.0, flags=None, ws=None, stream=None):
+    _check(load().teno_rhs(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter), _ptr(flags),
+                           _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "teno_rhs")
+
+
+def teno_rk3_step(p, U, dt=0.0, dt_device=None, ws=None, stream=None):
+    _check(load().teno_rk3_step(ctypes.byref(p), _ptr(U), float(dt), _ptr(dt_device), _ptr(ws),
+                                ws.numel() * ws.element_size(), _stream(stream)), "teno_rk3_step")
+
+
+def teno_cfl_dt(p, U, cfl, dt_device, ws=None, stream=None):
+    _check(load().teno_cfl_dt(ctypes.byref(p), _ptr(U), float(cfl), _ptr(dt_device), _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream(stream)), "teno_cfl_dt")
+
+
+def teno_status(ws, stream=None):
+    """Synchronise; return the non-physical count (and clear it)."""
+    n = ctypes.c_int64()
+    code = load().teno_status(_ptr(ws), _stream(stream), ctypes.byref(n))
+    if code not in (TENO_OK, TENO_ENONPHYSICAL):
+        raise TenoError(code, "teno_status")
+    return int(n.value)
+
+
+def teno_advance_host(p, U_host, U_dev, nsteps, cfl, ws, stream=None):
+    """U_host: contiguous CPU float64 tensor (pinned for full copy speed)."""
+    t = ctypes.c_double()
+    if U_host.is_cuda or not U_host.is_contiguous():
+        raise ValueError("U_host must be a contiguous CPU tensor")
+    _check(load().teno_advance_host(ctypes.byref(p), ctypes.c_void_p(U_host.data_ptr()),
+                                    _ptr(U_dev), int(nsteps), float(cfl), ctypes.byref(t),
+                                    _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_advance_host")
+    return t.value
+
+
+def teno_profile_enable(on: bool = True):
+    _check(load().teno_profile_enable(1 if on else 0), "teno_profile_enable")
+
+
+def teno_profile_read():
+    """(milliseconds, launches, faces) of the recorded face-sweep launches."""
+    ms = ctypes.c_double()
+    nl = ctypes.c_int64()
+    nf = ctypes.c_int64()
+    _check(load().teno_profile_read(ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nf)),
+           "teno_profile_read")
+    return ms.value, nl.value, nf.value
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Solver:
+    """Owns a workspace (and a device dt scalar) for one parameter set."""
+
+    def __init__(self, p: teno_params, device="cuda"):
+        import torch
+        self.p = p
+        self.device = torch.device(device)
+        nb = teno_workspace_bytes(p)
+        self.ws = torch.zeros((nb + 7) // 8, dtype=torch.float64, device=self.device)
+        self.dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.ncons = p.ndim + 2
+        self.ncells = p.n[0] * p.n[1] * p.n[2]
+
+    def rhs(self, U, dt_limiter=0.0, flags=False, stream=None):
+        import torch
+        out = torch.empty_like(U)
+        fl = None
+        if flags:
+            fl = torch.zeros(teno_flags_bytes(self.p), dtype=torch.uint8, device=self.device)
+        teno_rhs(self.p, U, out, dt_limiter, fl, self.ws, stream)
+        return (out, fl) if flags else out
+
+    def cfl_dt(self, U, cfl=0.4, stream=None):
+        teno_cfl_dt(self.p, U, cfl, self.dt, self.ws, stream)
+        return self.dt
+
+    def step(self, U, dt=None, stream=None):
+        """One RK3 step in place; dt=None uses the device scalar self.dt."""
+        if dt is None:
+            teno_rk3_step(self.p, U, 0.0, self.dt, self.ws, stream)
+        else:
+            teno_rk3_step(self.p, U, float(dt), None, self.ws, stream)
+
+    def status(self, stream=None):
+        return teno_status(self.ws, stream)

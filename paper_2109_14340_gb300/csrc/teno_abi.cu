@@ -1,0 +1,531 @@
+// C ABI of the TENO-AA library (declared in include/teno.h): parameter
+// validation, workspace layout, and the per-stage launch sequence
+//   [wave maxima] -> prepare -> face sweep x [-> y [-> z]] -> combine.
+#include <cstdio>
+#include <cstring>
+
+#include "teno.h"
+#include "teno_face.cuh"
+
+namespace teno {
+
+// Explicit instantiations live in teno_face8.cu / teno_face10.cu.
+cudaError_t launch_face8(int nd, int d, const FaceArgs &a, cudaStream_t s);
+cudaError_t launch_face10(int nd, int d, const FaceArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+
+struct CombineArgs {
+    const double *F[3];      // face fluxes per direction, [nc][nfaces_d]
+    int64_t nfaces[3];
+    int64_t fstride[3];      // face-grid stride of the sweep axis in grid d
+    double inv_dx[3];
+    const double *Uk;        // stage input (whose RHS the fluxes are)
+    const double *Un;        // state at t^n (RK modes)
+    double *out;             // rhs (mode 0) or next stage state
+    Status *st;
+    int64_t n[3];
+    int64_t ncell;
+    int mode;                // 0: rhs, 1..3: RK stage 0..2
+    Consts K;
+};
+
+// L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. approximateEq), then the
+// SSP-RK3 stage combination (Eq. Runge-kutta); counts non-physical cells of
+// the stage input.
+template <int ND>
+__global__ void combine_kernel(CombineArgs a)
+{
+    constexpr int nc = ND + 2;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < a.ncell;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = id % a.n[0], y = (id / a.n[0]) % a.n[1], z = id / (a.n[0] * a.n[1]);
+        int64_t flo[3];
+#pragma unroll
+        for (int d = 0; d < ND; d++) {
+            const int64_t fn0 = a.n[0] + (d == 0), fn1 = a.n[1] + (d == 1);
+            flo[d] = x + fn0 * (y + fn1 * z);
+        }
+        double Uc[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
+        {
+            CellQ<ND> q;
+            cell_quantities<ND, 0>(Uc, a.K, q);
+            if (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H))
+                atomicAdd(&a.st->nonphys, 1ull);
+        }
+        const double dt = a.st->dt;
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int d = 0; d < ND; d++) {
+                const double *Fd = a.F[d] + c * a.nfaces[d];
+                const double t = (Fd[flo[d] + a.fstride[d]] - Fd[flo[d]]) * a.inv_dx[d];
+                acc = acc - t;
+            }
+            double o;
+            if (a.mode == 0) {
+                o = acc;
+            } else {
+                const double t = Uc[c] + dt * acc;
+                if (a.mode == 1) o = t;
+                else if (a.mode == 2) o = 0.75 * a.Un[c * a.ncell + id] + 0.25 * t;
+                else o = (1.0 / 3.0) * a.Un[c * a.ncell + id] + (2.0 / 3.0) * t;
+            }
+            a.out[c * a.ncell + id] = o;
+        }
+    }
+}
+
+// A_d = max over cells of |u_d| + c, accumulated as bit patterns (the
+// ordering of non-negative doubles); NaN never enters.  Optionally counts
+// non-physical cells.
+template <int ND>
+__global__ void wave_max_kernel(const double *U, int64_t ncell, Consts K, Status *st, int count)
+{
+    constexpr int nc = ND + 2;
+    double m[ND];
+#pragma unroll
+    for (int d = 0; d < ND; d++) m[d] = 0.0;
+    unsigned long long bad = 0;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < ncell;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        double Uc[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Uc[c] = U[c * ncell + id];
+        CellQ<ND> q;
+        cell_quantities<ND, 0>(Uc, K, q);
+        if (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H)) bad++;
+#pragma unroll
+        for (int d = 0; d < ND; d++) {
+            const double e = fabs(q.u[d]) + q.c;
+            if (e > m[d]) m[d] = e;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        double v = m[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            if (w > v) v = w;
+        }
+        if ((threadIdx.x & 31) == 0 && v > 0.0)
+            atomicMax(&st->amax[d], (unsigned long long)__double_as_longlong(v));
+    }
+    if (count) {
+        for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, o);
+        if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&st->nonphys, bad);
+    }
+}
+
+// dt = cfl / sum_d A_d / dx_d (written to *dt_out and the status block).
+__global__ void cfl_finalize_kernel(Status *st, int nd, double cfl, double3 inv_dx, double *dt_out,
+                                    int accumulate)
+{
+    const double idx[3] = {inv_dx.x, inv_dx.y, inv_dx.z};
+    double S = __longlong_as_double((long long)st->amax[0]) * idx[0];
+    for (int d = 1; d < nd; d++) S = S + __longlong_as_double((long long)st->amax[d]) * idx[d];
+    const double dt = cfl / S;
+    st->dt = dt;
+    if (dt_out) *dt_out = dt;
+    if (accumulate) st->t_accum = st->t_accum + dt;
+}
+
+// Stage preparation: dt from the host value or a device scalar, and the
+// limiter's effective dt/dx per direction: dt/dx in 1D; (dt S) / A_d with
+// S = sum_d A_d/dx_d in several dimensions (each direction's one-sided
+// updates get the share A_d/dx_d / S of the update).
+__global__ void prepare_kernel(Status *st, int nd, double dt_host, const double *dt_dev,
+                               double3 inv_dx, int limiter)
+{
+    const double dt = dt_dev ? *dt_dev : dt_host;
+    st->dt = dt;
+    if (!limiter) return;
+    const double idx[3] = {inv_dx.x, inv_dx.y, inv_dx.z};
+    if (nd == 1) {
+        st->lam[0] = dt * idx[0];
+        return;
+    }
+    double A[3];
+    for (int d = 0; d < nd; d++) A[d] = __longlong_as_double((long long)st->amax[d]);
+    double S = A[0] * idx[0];
+    for (int d = 1; d < nd; d++) S = S + A[d] * idx[d];
+    for (int d = 0; d < nd; d++) st->lam[d] = (dt * S) / A[d];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+static int ncons(const teno_params *p) { return p->ndim + 2; }
+
+static int64_t ncells(const teno_params *p) { return p->n[0] * p->n[1] * p->n[2]; }
+
+static int64_t face_grid(const teno_params *p, int d)
+{
+    int64_t s = 1;
+    for (int a = 0; a < 3; a++) s *= (a == d) ? p->n[a] + 1 : p->n[a];
+    return s;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t status, flux[3], stage, total;
+};
+
+static Layout layout(const teno_params *p)
+{
+    Layout L;
+    const int nc = ncons(p);
+    size_t off = 0;
+    L.status = off;
+    off += align256(sizeof(Status));
+    for (int d = 0; d < 3; d++) {
+        L.flux[d] = off;
+        if (d < p->ndim) off += align256(sizeof(double) * (size_t)nc * face_grid(p, d));
+    }
+    L.stage = off;
+    off += align256(sizeof(double) * (size_t)nc * ncells(p));
+    L.total = off;
+    return L;
+}
+
+static int validate(const teno_params *p)
+{
+    if (!p) return TENO_EINVAL;
+    if (p->ndim < 1 || p->ndim > 3) return TENO_EINVAL;
+    if (p->scheme != 8 && p->scheme != 10) return TENO_EINVAL;
+    if (p->flux_split != TENO_SPLIT_LLF && p->flux_split != TENO_SPLIT_RUSANOV) return TENO_EINVAL;
+    if (p->limiter != 0 && p->limiter != 1) return TENO_EINVAL;
+    if (p->q != 7 || p->reserved != 0) return TENO_EINVAL;
+    if (!(p->gamma > 1.0) || !(p->ct_cr > 0.0) || !(p->eps_beta >= 0.0) || !(p->eps_eta > 0.0))
+        return TENO_EINVAL;
+    if (!(p->ct_alpha1 >= 0.0) || !(p->ct_alpha2 >= 0.0) || !(p->limiter_eps >= 0.0))
+        return TENO_EINVAL;
+    const int H = p->scheme / 2;
+    for (int a = 0; a < 3; a++) {
+        if (a < p->ndim) {
+            if (p->n[a] < H || p->n[a] > (int64_t)1 << 31) return TENO_EINVAL;
+            if (!(p->dx[a] > 0.0)) return TENO_EINVAL;
+            for (int side = 0; side < 2; side++) {
+                const int b = side ? p->bc_hi[a] : p->bc_lo[a];
+                if (b < TENO_BC_PERIODIC || b > TENO_BC_SLIPWALL) return TENO_EINVAL;
+            }
+            if ((p->bc_lo[a] == TENO_BC_PERIODIC) != (p->bc_hi[a] == TENO_BC_PERIODIC))
+                return TENO_EINVAL;
+        } else if (p->n[a] != 1) {
+            return TENO_EINVAL;
+        }
+    }
+    if (p->n[1] > 65535 || p->n[2] > 65535 * 8) return TENO_EINVAL;   // grid limits
+    return TENO_OK;
+}
+
+static int check_ptr(const void *ptr, bool nullable = false)
+{
+    if (!ptr) return nullable ? TENO_OK : TENO_EINVAL;
+    return ((uintptr_t)ptr & 15) ? TENO_EINVAL : TENO_OK;
+}
+
+static Consts consts_of(const teno_params *p)
+{
+    Consts K;
+    K.gamma = p->gamma;
+    K.gm1 = p->gamma - 1.0;
+    K.alpha1 = p->ct_alpha1;
+    K.alpha2 = p->ct_alpha2;
+    K.cr = p->ct_cr;
+    K.eps_beta = p->eps_beta;
+    K.eps_eta = p->eps_eta;
+    K.lim_eps = p->limiter_eps;
+    K.split = p->flux_split;
+    K.limiter = p->limiter;
+    return K;
+}
+
+static double3 inv_dx_of(const teno_params *p)
+{
+    return make_double3(1.0 / p->dx[0], 1.0 / p->dx[1], 1.0 / p->dx[2]);
+}
+
+static int grid_for(int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+#define CUDA_TRY(x)                                   \
+    do {                                              \
+        if ((x) != cudaSuccess) return TENO_ECUDA;    \
+    } while (0)
+
+static cudaError_t launch_wave_max(const teno_params *p, const double *U, Status *st,
+                                   int count, cudaStream_t s)
+{
+    const Consts K = consts_of(p);
+    const int64_t N = ncells(p);
+    const int blk = 256, grd = grid_for(N, blk);
+    cudaError_t e = cudaMemsetAsync(st->amax, 0, sizeof(st->amax), s);
+    if (e != cudaSuccess) return e;
+    if (p->ndim == 1) wave_max_kernel<1><<<grd, blk, 0, s>>>(U, N, K, st, count);
+    else if (p->ndim == 2) wave_max_kernel<2><<<grd, blk, 0, s>>>(U, N, K, st, count);
+    else wave_max_kernel<3><<<grd, blk, 0, s>>>(U, N, K, st, count);
+    return cudaGetLastError();
+}
+
+// Event record of the face-sweep launches (teno_profile_*).
+struct ProfileRecord {
+    bool on = false;
+    int used = 0;
+    int64_t faces = 0;
+    static constexpr int kMax = 8192;
+    cudaEvent_t ev[2 * kMax];
+    int64_t nf[kMax];
+    int created = 0;
+};
+static ProfileRecord g_prof;
+
+static cudaError_t profile_mark(int which, int slot, cudaStream_t s)
+{
+    const int k = 2 * slot + which;
+    while (g_prof.created <= k) {
+        cudaError_t e = cudaEventCreate(&g_prof.ev[g_prof.created]);
+        if (e != cudaSuccess) return e;
+        g_prof.created++;
+    }
+    return cudaEventRecord(g_prof.ev[k], s);
+}
+
+// One right-hand-side evaluation of Uk into the face buffers, then combine.
+static int stage(const teno_params *p, const double *Uk, const double *Un, double *out, int mode,
+                 double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s)
+{
+    const Layout L = layout(p);
+    Status *st = (Status *)(ws + L.status);
+    const Consts K = consts_of(p);
+    const double3 idx = inv_dx_of(p);
+    const int nd = p->ndim, nc = ncons(p);
+    if (p->limiter && nd > 1) CUDA_TRY(launch_wave_max(p, Uk, st, 0, s));
+    prepare_kernel<<<1, 1, 0, s>>>(st, nd, dt_host, dt_dev, idx, p->limiter);
+    CUDA_TRY(cudaGetLastError());
+    uint8_t *fl = flags;
+    for (int d = 0; d < nd; d++) {
+        FaceArgs a;
+        a.U = Uk;
+        a.F = (double *)(ws + L.flux[d]);
+        a.flags = fl;
+        a.st = st;
+        for (int k = 0; k < 3; k++) a.n[k] = p->n[k];
+        a.ncell = ncells(p);
+        a.nfaces = face_grid(p, d);
+        a.bc_lo = p->bc_lo[d];
+        a.bc_hi = p->bc_hi[d];
+        a.K = K;
+        const int slot = (g_prof.on && g_prof.used < ProfileRecord::kMax) ? g_prof.used++ : -1;
+        if (slot >= 0) {
+            g_prof.nf[slot] = a.nfaces;
+            CUDA_TRY(profile_mark(0, slot, s));
+        }
+        cudaError_t e = (p->scheme == 8) ? launch_face8(nd, d, a, s) : launch_face10(nd, d, a, s);
+        if (e != cudaSuccess) return TENO_ECUDA;
+        if (slot >= 0) CUDA_TRY(profile_mark(1, slot, s));
+        if (fl) fl += (size_t)face_grid(p, d) * nc * 2;
+    }
+    CombineArgs c;
+    for (int d = 0; d < 3; d++) {
+        c.F[d] = (const double *)(ws + L.flux[d]);
+        c.nfaces[d] = d < nd ? face_grid(p, d) : 0;
+        const int64_t fn0 = p->n[0] + (d == 0), fn1 = p->n[1] + (d == 1);
+        c.fstride[d] = d == 0 ? 1 : (d == 1 ? fn0 : fn0 * fn1);
+    }
+    c.inv_dx[0] = idx.x; c.inv_dx[1] = idx.y; c.inv_dx[2] = idx.z;
+    c.Uk = Uk;
+    c.Un = Un;
+    c.out = out;
+    c.st = st;
+    for (int k = 0; k < 3; k++) c.n[k] = p->n[k];
+    c.ncell = ncells(p);
+    c.mode = mode;
+    c.K = K;
+    const int blk = 256, grd = grid_for(c.ncell, blk);
+    if (nd == 1) combine_kernel<1><<<grd, blk, 0, s>>>(c);
+    else if (nd == 2) combine_kernel<2><<<grd, blk, 0, s>>>(c);
+    else combine_kernel<3><<<grd, blk, 0, s>>>(c);
+    CUDA_TRY(cudaGetLastError());
+    return TENO_OK;
+}
+
+}  // namespace teno
+
+using namespace teno;
+
+extern "C" {
+
+void teno_params_init(teno_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->ndim = 1;
+    p->scheme = 8;
+    p->flux_split = TENO_SPLIT_LLF;
+    p->limiter = 0;
+    p->n[0] = p->n[1] = p->n[2] = 1;
+    p->dx[0] = p->dx[1] = p->dx[2] = 1.0;
+    p->gamma = 1.4;
+    p->ct_alpha1 = 14.0;
+    p->ct_alpha2 = 6.4;
+    p->ct_cr = 0.265;
+    p->eps_beta = 1e-40;
+    p->eps_eta = 1e-40;
+    p->limiter_eps = 1e-13;
+    p->q = 7;
+}
+
+int teno_workspace_bytes(const teno_params *p, size_t *bytes)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (!bytes) return TENO_EINVAL;
+    *bytes = layout(p).total;
+    return TENO_OK;
+}
+
+int teno_flags_bytes(const teno_params *p, size_t *bytes)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (!bytes) return TENO_EINVAL;
+    size_t t = 0;
+    for (int d = 0; d < p->ndim; d++) t += (size_t)face_grid(p, d) * ncons(p) * 2;
+    *bytes = t;
+    return TENO_OK;
+}
+
+int teno_rhs(const teno_params *p, const double *U, double *rhs, double dt_limiter,
+             uint8_t *flags, void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(rhs) || check_ptr(ws)) return TENO_EINVAL;
+    if (U == rhs) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total) return TENO_EINVAL;
+    if (p->limiter && !(dt_limiter >= 0.0)) return TENO_EINVAL;
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)ws, (cudaStream_t)stream);
+}
+
+int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_device,
+                  void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(ws) || ((uintptr_t)dt_device & 7)) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total) return TENO_EINVAL;
+    if (!dt_device && !(dt >= 0.0)) return TENO_EINVAL;
+    const Layout L = layout(p);
+    double *Us = (double *)((char *)ws + L.stage);
+    cudaStream_t s = (cudaStream_t)stream;
+    // U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U = 1/3 U + 2/3 (U2 + dt L(U2))
+    if ((r = stage(p, U, U, Us, 1, dt, dt_device, nullptr, (char *)ws, s))) return r;
+    if ((r = stage(p, Us, U, Us, 2, dt, dt_device, nullptr, (char *)ws, s))) return r;
+    return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s);
+}
+
+int teno_cfl_dt(const teno_params *p, const double *U, double cfl, double *dt_device,
+                void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(ws) || ((uintptr_t)dt_device & 7)) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total || !(cfl > 0.0)) return TENO_EINVAL;
+    Status *st = (Status *)((char *)ws + layout(p).status);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(launch_wave_max(p, U, st, 0, s));
+    cfl_finalize_kernel<<<1, 1, 0, s>>>(st, p->ndim, cfl, inv_dx_of(p), dt_device, 0);
+    CUDA_TRY(cudaGetLastError());
+    return TENO_OK;
+}
+
+int teno_status(void *ws, void *stream, int64_t *nonphysical)
+{
+    if (check_ptr(ws)) return TENO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Status *st = (Status *)ws;
+    unsigned long long v = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, &st->nonphys, sizeof(v), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemsetAsync(&st->nonphys, 0, sizeof(v), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (nonphysical) *nonphysical = (int64_t)v;
+    return v ? TENO_ENONPHYSICAL : TENO_OK;
+}
+
+int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int nsteps,
+                      double cfl, double *t_host, void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (!U_host || check_ptr(U_dev) || check_ptr(ws) || nsteps < 0 || !(cfl > 0.0))
+        return TENO_EINVAL;
+    if (ws_bytes < layout(p).total) return TENO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Status *st = (Status *)((char *)ws + layout(p).status);
+    const size_t bytes = sizeof(double) * (size_t)ncons(p) * ncells(p);
+    CUDA_TRY(cudaMemcpyAsync(U_dev, U_host, bytes, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(&st->t_accum, 0, sizeof(double), s));
+    for (int k = 0; k < nsteps; k++) {
+        CUDA_TRY(launch_wave_max(p, U_dev, st, 0, s));
+        cfl_finalize_kernel<<<1, 1, 0, s>>>(st, p->ndim, cfl, inv_dx_of(p), nullptr, 1);
+        CUDA_TRY(cudaGetLastError());
+        if ((r = teno_rk3_step(p, U_dev, 0.0, &st->dt, ws, ws_bytes, stream))) return r;
+    }
+    CUDA_TRY(cudaMemcpyAsync(U_host, U_dev, bytes, cudaMemcpyDeviceToHost, s));
+    double t = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&t, &st->t_accum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (t_host) *t_host = t;
+    return TENO_OK;
+}
+
+int teno_profile_enable(int on)
+{
+    g_prof.on = on != 0;
+    g_prof.used = 0;
+    return TENO_OK;
+}
+
+int teno_profile_read(double *ms, int64_t *launches, int64_t *faces)
+{
+    double tot = 0.0;
+    int64_t nf = 0;
+    for (int i = 0; i < g_prof.used; i++) {
+        CUDA_TRY(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
+        tot += t;
+        nf += g_prof.nf[i];
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = g_prof.used;
+    if (faces) *faces = nf;
+    return TENO_OK;
+}
+
+const char *teno_strerror(int code)
+{
+    switch (code) {
+    case TENO_OK: return "ok";
+    case TENO_EINVAL: return "invalid parameter, pointer, size or alignment";
+    case TENO_ECUDA: return "CUDA runtime error";
+    case TENO_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0, non-finite value or "
+                                   "non-positive Roe sound speed squared)";
+    case TENO_ETIMEOUT: return "bounded device wait timed out";
+    default: return "unknown error code";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+// Device building blocks of the TENO-AA Euler right-hand side (sm_103a, FP64).
+//
+// Every expression fixes its evaluation order; the library is compiled with
+// --fmad=false so that the only fused multiply-adds are the explicit fma()
+// calls.  Division and sqrt of doubles are IEEE round-to-nearest on the GPU.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "teno_coeffs.cuh"
+
+namespace teno {
+
+// Workspace header (first 256 bytes of every workspace).
+struct Status {
+    unsigned long long nonphys;    // non-physical cells + faces (teno_status)
+    unsigned long long amax[3];    // bit patterns of A_d = max(|u_d| + c) >= 0
+    double dt;                     // time step of the current call
+    double lam[3];                 // limiter: effective dt/dx of each direction
+    double t_accum;                // summed dt of teno_advance_host
+    double pad[23];
+};
+static_assert(sizeof(Status) == 256, "status block is 256 bytes");
+
+// Optimal linear schemes on the large stencils (Sec. 4.1, Eqs. 6-, 8-,
+// 10-point), ascending offsets -2..3, -3..4, -4..5.
+static __constant__ double TENO_LIN3[6] = {
+    0.02852274270130377, -0.1714015614372447, 0.650378818735941,
+    0.6253788187359414, -0.1589015614372448, 0.02602274270130375};
+static __constant__ double TENO_LIN4[8] = {
+    -0.006866688980568011, 0.05128582585522106, -0.1968478198727312,
+    0.6552858258552222, 0.6452858258552218, -0.1908478198727314,
+    0.04928582585522098, -0.006580974694853729};
+static __constant__ double TENO_LIN5[10] = {
+    0.001911786299492748, -0.0170332977472532, 0.07339445614860979,
+    -0.221228429084247, 0.6657332621611695, 0.6557332621611695,
+    -0.2145617624175796, 0.07053731329146805, -0.01631901203296621,
+    0.001832421220128962};
+// Optimal weights of the small stencils S0, S1, S2 (Sec. 4.1).
+static __constant__ double TENO_DK[3] = {0.5065006634, 0.3699651429, 0.1235341937};
+// C_T = 10^-[beta] (Eq. CT_definition), [beta] clamped to 0..22.
+static __constant__ double TENO_TENPOW[23] = {
+    1e0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11,
+    1e-12, 1e-13, 1e-14, 1e-15, 1e-16, 1e-17, 1e-18, 1e-19, 1e-20, 1e-21, 1e-22};
+
+// Scheme constants passed by value to every kernel.
+struct Consts {
+    double gamma, gm1;
+    double alpha1, alpha2, cr, eps_beta, eps_eta, lim_eps;
+    int split, limiter;
+};
+
+// ---------------------------------------------------------------------------
+// Scalar TENO-AA reconstruction at face i+1/2 (Sec. 3.2-3.4, Sec. 4.2-4.3).
+// v[m + H - 1] holds offset m = -H+1 .. H from the upwind cell i.
+// ---------------------------------------------------------------------------
+
+// Eq. scale_separation with q = 7.
+__device__ __forceinline__ double scale_sep(double beta, double eps)
+{
+    double x = beta + eps;
+    double x2 = x * x;
+    double x4 = x2 * x2;
+    double x7 = (x4 * x2) * x;
+    return 1.0 / x7;
+}
+
+// Smoothness indicator of the large stencil S_L (Eq. TENO10_AA quadratic
+// forms) on data shifted by the cell-i value; terms of the zero shifted value
+// are skipped (they add exact zeros).
+template <int H, int L>
+__device__ __forceinline__ double beta_large(const double (&v)[2 * H])
+{
+    constexpr int lo = (L == 3) ? -2 : (L == 4 ? -3 : -4);
+    constexpr int w = 2 * L;
+    const double v0 = v[H - 1];
+    double s[w];
+#pragma unroll
+    for (int r = 0; r < w; r++) s[r] = v[lo + r + H - 1] - v0;
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < w; r++) {
+        if (r + lo == 0) continue;                // s == 0: contributes nothing
+        double coef_rr = (L == 3) ? TENO_Q6[r][r] : (L == 4 ? TENO_Q8[r][r] : TENO_Q10[r][r]);
+        double inner = coef_rr * s[r];
+#pragma unroll
+        for (int c = r + 1; c < w; c++) {
+            if (c + lo == 0) continue;
+            double cf = (L == 3) ? TENO_Q6[r][c] : (L == 4 ? TENO_Q8[r][c] : TENO_Q10[r][c]);
+            inner = fma(cf, s[c], inner);
+        }
+        acc = (r == 0) ? s[r] * inner : fma(s[r], inner, acc);
+    }
+    return acc;
+}
+
+template <int H, int L>
+__device__ __forceinline__ double flux_large(const double (&v)[2 * H])
+{
+    constexpr int lo = (L == 3) ? -2 : (L == 4 ? -3 : -4);
+    constexpr int w = 2 * L;
+    double c0 = (L == 3) ? TENO_LIN3[0] : (L == 4 ? TENO_LIN4[0] : TENO_LIN5[0]);
+    double acc = c0 * v[lo + H - 1];
+#pragma unroll
+    for (int r = 1; r < w; r++) {
+        double cr = (L == 3) ? TENO_LIN3[r] : (L == 4 ? TENO_LIN4[r] : TENO_LIN5[r]);
+        acc = fma(cr, v[lo + r + H - 1], acc);
+    }
+    return acc;
+}
+
+// [beta] of Eq. CT_definition from the first-order undivided differences
+// (Eq. m_definition), clamped to the power table.
+template <int H>
+__device__ __forceinline__ int ct_exponent(const double (&v)[2 * H], const Consts &K)
+{
+#define V(m) v[(m) + H - 1]
+    double dl[5];
+#pragma unroll
+    for (int m = -2; m <= 2; m++) dl[m + 2] = V(m + 1) - V(m);
+    double emin = 0.0;
+#pragma unroll
+    for (int j = -1; j <= 2; j++) {
+        double dp = dl[j + 2], dm = dl[j + 1];
+        double num = fabs((2.0 * dp) * dm) + K.eps_eta;
+        double den = (dp * dp + dm * dm) + K.eps_eta;
+        double e = num / den;
+        if (j == -1 || e < emin) emin = e;
+    }
+    double r = emin / K.cr;
+    double m = 1.0 - (r < 1.0 ? r : 1.0);
+    double om = 1.0 - m;
+    double om2 = om * om;
+    double g = (om2 * om2) * (1.0 + 4.0 * m);
+    double bct = K.alpha1 - K.alpha2 * (1.0 - g);
+    double fl = floor(bct);
+    return fl < 0.0 ? 0 : (fl > 22.0 ? 22 : (int)fl);
+#undef V
+}
+
+// One reconstruction; flag: bits 0-1 selected large stencil (L-2) or 0 for the
+// small-stencil fallback, bits 2-4 deltas of S0..S2 (fallback), bits 5-7 C_T
+// exponent minus 7.
+template <int H>
+__device__ __forceinline__ double teno_recon(const double (&v)[2 * H], const Consts &K,
+                                             uint8_t &flag)
+{
+#define V(m) v[(m) + H - 1]
+    const int nexp = ct_exponent<H>(v, K);
+    const double CT = TENO_TENPOW[nexp];
+    const uint8_t fct = (uint8_t)(((nexp - 7) & 7) << 5);
+
+    double a0 = V(-1) - V(1);
+    double b0 = (V(-1) - 2.0 * V(0)) + V(1);
+    double beta0 = 0.25 * (a0 * a0) + (13.0 / 12.0) * (b0 * b0);
+    double a1 = (3.0 * V(0) - 4.0 * V(1)) + V(2);
+    double b1 = (V(0) - 2.0 * V(1)) + V(2);
+    double beta1 = 0.25 * (a1 * a1) + (13.0 / 12.0) * (b1 * b1);
+    double a2 = (V(-2) - 4.0 * V(-1)) + 3.0 * V(0);
+    double b2 = (V(-2) - 2.0 * V(-1)) + V(0);
+    double beta2 = 0.25 * (a2 * a2) + (13.0 / 12.0) * (b2 * b2);
+    double g0 = scale_sep(beta0, K.eps_beta);
+    double g1 = scale_sep(beta1, K.eps_beta);
+    double g2 = scale_sep(beta2, K.eps_beta);
+    double g012 = (g0 + g1) + g2;
+
+    // Targeted ENO-like selection (Sec. 3.3), largest group first.
+    if (H == 5) {
+        double g5 = scale_sep(beta_large<H, 5>(v), K.eps_beta);
+        double chi = g5 / (g012 + g5);
+        if (!(chi < CT)) { flag = (uint8_t)(3 | fct); return flux_large<H, 5>(v); }
+    }
+    {
+        double g4 = scale_sep(beta_large<H, 4>(v), K.eps_beta);
+        double chi = g4 / (g012 + g4);
+        if (!(chi < CT)) { flag = (uint8_t)(2 | fct); return flux_large<H, 4>(v); }
+    }
+    {
+        double g3 = scale_sep(beta_large<H, 3>(v), K.eps_beta);
+        double chi = g3 / (g012 + g3);
+        if (!(chi < CT)) { flag = (uint8_t)(1 | fct); return flux_large<H, 3>(v); }
+    }
+
+    // Small-stencil fallback (Eq. renormalize, Eq. reconstuction), normalised
+    // over S0, S1, S2.
+    double s = g012;
+    int d0 = !(g0 / s < CT), d1 = !(g1 / s < CT), d2 = !(g2 / s < CT);
+    double dd0 = d0 ? TENO_DK[0] : 0.0, dd1 = d1 ? TENO_DK[1] : 0.0, dd2 = d2 ? TENO_DK[2] : 0.0;
+    double den = (dd0 + dd1) + dd2;
+    double w0 = dd0 / den, w1 = dd1 / den, w2 = dd2 / den;
+    double f0 = ((-V(-1) + 5.0 * V(0)) + 2.0 * V(1)) / 6.0;
+    double f1 = ((2.0 * V(0) + 5.0 * V(1)) - V(2)) / 6.0;
+    double f2 = ((2.0 * V(-2) - 7.0 * V(-1)) + 11.0 * V(0)) / 6.0;
+    double fh = w0 * f0;
+    fh = fma(w1, f1, fh);
+    fh = fma(w2, f2, fh);
+    flag = (uint8_t)(((d0 | (d1 << 1) | (d2 << 2)) << 2) | fct);
+    return fh;
+#undef V
+}
+
+// ---------------------------------------------------------------------------
+// Euler: primitive variables and physical flux of one cell (Eq. Euler, EOS).
+// ---------------------------------------------------------------------------
+
+template <int ND>
+struct CellQ {
+    double U[ND + 2], F[ND + 2];
+    double u[ND];
+    double p, c, H, sr;
+};
+
+template <int ND, int D>
+__device__ __forceinline__ void cell_quantities(const double (&Uc)[ND + 2], const Consts &K,
+                                                CellQ<ND> &q)
+{
+    constexpr int nc = ND + 2;
+#pragma unroll
+    for (int c = 0; c < nc; c++) q.U[c] = Uc[c];
+    double rho = Uc[0], E = Uc[nc - 1];
+    double rinv = 1.0 / rho;
+#pragma unroll
+    for (int a = 0; a < ND; a++) q.u[a] = Uc[1 + a] * rinv;
+    double t = Uc[1] * q.u[0];
+#pragma unroll
+    for (int a = 1; a < ND; a++) t = fma(Uc[1 + a], q.u[a], t);
+    double ke = 0.5 * t;
+    q.p = K.gm1 * (E - ke);
+    q.c = sqrt((K.gamma * q.p) * rinv);
+    double Ep = E + q.p;
+    q.H = Ep * rinv;
+    q.sr = sqrt(rho);
+    double md = Uc[1 + D];
+    q.F[0] = md;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        q.F[1 + a] = md * q.u[a];
+        if (a == D) q.F[1 + a] = q.F[1 + a] + q.p;
+    }
+    q.F[nc - 1] = q.u[D] * Ep;
+}
+
+// Pressure of a conserved state (used by the limiter).
+template <int ND>
+__device__ __forceinline__ double pressure_of(const double (&Uc)[ND + 2], double gm1)
+{
+    double rinv = 1.0 / Uc[0];
+    double t = Uc[1] * (Uc[1] * rinv);
+#pragma unroll
+    for (int a = 1; a < ND; a++) t = fma(Uc[1 + a], Uc[1 + a] * rinv, t);
+    return gm1 * (Uc[ND + 1] - 0.5 * t);
+}
+
+// ---------------------------------------------------------------------------
+// Roe average (Sec. 5) and eigenvectors of dF_D/dU.  Field order: u-c,
+// entropy, shear waves (tangential axes ascending), u+c.
+// ---------------------------------------------------------------------------
+template <int ND, int D>
+__device__ __forceinline__ double roe_eigensystem(const double (&ul)[ND], double Hl, double sl,
+                                                  const double (&ur)[ND], double Hr, double sr,
+                                                  double gm1, double (&Lm)[ND + 2][ND + 2],
+                                                  double (&Rm)[ND + 2][ND + 2])
+{
+    constexpr int nc = ND + 2, last = nc - 1;
+    double inv = 1.0 / (sl + sr);
+    double ut[ND];
+#pragma unroll
+    for (int a = 0; a < ND; a++) ut[a] = fma(sr, ur[a], sl * ul[a]) * inv;
+    double Ht = fma(sr, Hr, sl * Hl) * inv;
+    double q2 = ut[0] * ut[0];
+#pragma unroll
+    for (int a = 1; a < ND; a++) q2 = fma(ut[a], ut[a], q2);
+    double c2 = gm1 * (Ht - 0.5 * q2);
+    double ct = sqrt(c2);
+    double cinv = 1.0 / ct;
+    double b1 = gm1 * (cinv * cinv);
+    double b2 = (0.5 * q2) * b1;
+    double un = ut[D];
+    double unc = un * cinv;
+    double bu = b1 * un;
+    double unct = un * ct;
+#pragma unroll
+    for (int r = 0; r < nc; r++)
+#pragma unroll
+        for (int c = 0; c < nc; c++) { Lm[r][c] = 0.0; Rm[r][c] = 0.0; }
+    Lm[0][0] = 0.5 * (b2 + unc);
+    Lm[last][0] = 0.5 * (b2 - unc);
+    Lm[1][0] = 1.0 - b2;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        double ba = b1 * ut[a];
+        if (a == D) {
+            Lm[0][1 + a] = 0.5 * (-bu - cinv);
+            Lm[last][1 + a] = 0.5 * (cinv - bu);
+        } else {
+            Lm[0][1 + a] = 0.5 * (-ba);
+            Lm[last][1 + a] = 0.5 * (-ba);
+        }
+        Lm[1][1 + a] = ba;
+    }
+    Lm[0][last] = 0.5 * b1;
+    Lm[last][last] = 0.5 * b1;
+    Lm[1][last] = -b1;
+    Rm[0][0] = 1.0; Rm[0][1] = 1.0; Rm[0][last] = 1.0;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        Rm[1 + a][0] = (a == D) ? un - ct : ut[a];
+        Rm[1 + a][1] = ut[a];
+        Rm[1 + a][last] = (a == D) ? un + ct : ut[a];
+    }
+    Rm[last][0] = Ht - unct;
+    Rm[last][1] = 0.5 * q2;
+    Rm[last][last] = Ht + unct;
+    int k = 2;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        if (a == D) continue;
+        Lm[k][0] = -ut[a];
+        Lm[k][1 + a] = 1.0;
+        Rm[1 + a][k] = 1.0;
+        Rm[last][k] = ut[a];
+        k++;
+    }
+    return c2;
+}
+
+}  // namespace teno

@@ -1,0 +1,266 @@
+// Face-flux sweep along one direction: for every face i+1/2 of the face grid,
+// Roe average -> eigenvectors -> characteristic projection of the 2H-cell
+// stencil -> LLF/Rusanov split -> TENO-AA reconstruction of f+ and f- per
+// field -> back-projection -> positivity limiter (arXiv 2109.14340, Sec. 3-5).
+//
+// Tiling: a block owns TF consecutive faces along the sweep axis D for TP
+// pencils adjacent in x.  It stages the TF + 2H - 1 cells those faces touch
+// (ghost cells resolved by the boundary rules of App. A) in shared memory as
+// per-cell primitive quantities, then one thread computes one face.
+#pragma once
+
+#include "teno_dev.cuh"
+
+namespace teno {
+
+struct FaceArgs {
+    const double *U;       // state, [nc][ncell]
+    double *F;             // face fluxes of direction D, [nc][nfaces]
+    uint8_t *flags;        // decision record of direction D or nullptr
+    Status *st;
+    int64_t n[3];
+    int64_t ncell, nfaces;
+    int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
+    Consts K;
+};
+
+// App. A ghost-cell rules along one axis; mir = slip-wall mirror.  The final
+// clamp only matters for padding cells beyond the last face of a tile.
+__device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int lo, int hi, bool &mir)
+{
+    mir = false;
+    int64_t r = j;
+    if (j < 0) {
+        if (lo == 0) r = ((j % n) + n) % n;
+        else if (lo == 1) r = 0;
+        else { mir = true; r = -j - 1; }
+    } else if (j >= n) {
+        if (hi == 0) r = j % n;
+        else if (hi == 1) r = n - 1;
+        else { mir = true; r = 2 * n - 1 - j; }
+    }
+    return r < 0 ? 0 : (r >= n ? n - 1 : r);
+}
+
+template <int ND>
+struct SmemLayout {
+    static constexpr int nc = ND + 2;
+    static constexpr int QU = 0, QF = nc, QV = 2 * nc;           // U, F, velocity
+    static constexpr int QH = QV + ND, QSR = QH + 1, QC = QH + 2;  // enthalpy, sqrt(rho), c
+    static constexpr int QLM = QH + 3, QL0 = QLM + 1, QLP = QLM + 2, QLR = QLM + 3;
+    static constexpr int NQ = QLR + 1;
+};
+
+template <int ND, int H, int TP, int TF>
+constexpr size_t face_smem_bytes()
+{
+    return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP;
+}
+
+template <int ND, int H, int D, int TP, int TF>
+__global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
+{
+    using SL = SmemLayout<ND>;
+    constexpr int nc = ND + 2, last = nc - 1, W = 2 * H;
+    constexpr int NS = TF + 2 * H - 1;
+    extern __shared__ double sm[];
+#define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
+
+    const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
+    int64_t x0 = 0, y = 0, z = 0, f0;
+    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = blockIdx.y; z = blockIdx.z; }
+    else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
+    else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
+
+    // Stage cells f0-H .. f0+TF+H-2 along D.
+    for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
+        const int j = idx / TP, p = idx % TP;
+        const int64_t xg = x0 + p;
+        if (D != 0 && xg >= n0) continue;
+        bool mir;
+        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, mir);
+        int64_t id;
+        if (D == 0) id = gi + n0 * (y + n1 * z);
+        else if (D == 1) id = xg + n0 * (gi + n1 * z);
+        else id = xg + n0 * (y + n1 * gi);
+        double Uc[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
+        if (mir) Uc[1 + D] = -Uc[1 + D];
+        CellQ<ND> q;
+        cell_quantities<ND, D>(Uc, a.K, q);
+#pragma unroll
+        for (int c = 0; c < nc; c++) { SQ(SL::QU + c, j, p) = q.U[c]; SQ(SL::QF + c, j, p) = q.F[c]; }
+#pragma unroll
+        for (int k = 0; k < ND; k++) SQ(SL::QV + k, j, p) = q.u[k];
+        SQ(SL::QH, j, p) = q.H;
+        SQ(SL::QSR, j, p) = q.sr;
+        SQ(SL::QC, j, p) = q.c;
+        const double vd = q.u[D], cj = q.c;
+        SQ(SL::QLM, j, p) = fabs(vd - cj);
+        SQ(SL::QL0, j, p) = fabs(vd);
+        SQ(SL::QLP, j, p) = fabs(vd + cj);
+        SQ(SL::QLR, j, p) = fabs(vd) + cj;
+    }
+    __syncthreads();
+
+    const int p = threadIdx.x % TP, fo = threadIdx.x / TP;
+    const int64_t f = f0 + fo;
+    if (f > nD || (D != 0 && x0 + p >= n0)) return;
+    const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
+
+    // Roe average and eigenvectors (Sec. 5).
+    double ul[ND], ur[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) { ul[k] = SQ(SL::QV + k, jl, p); ur[k] = SQ(SL::QV + k, jr, p); }
+    double Lm[nc][nc], Rm[nc][nc];
+    const double c2 = roe_eigensystem<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
+                                             SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
+    if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
+
+    // Splitting speeds over the stencil.
+    double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
+#pragma unroll
+    for (int j = 0; j < W; j++) {
+        const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
+        const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
+        if (j == 0 || em > am) am = em;
+        if (j == 0 || e0 > a0) a0 = e0;
+        if (j == 0 || ep > ap) ap = ep;
+        if (j == 0 || er > ar) ar = er;
+    }
+
+    int64_t flin;
+    if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
+    else if (D == 1) flin = x0 + p + n0 * (f + (n1 + 1) * z);
+    else flin = x0 + p + n0 * (y + n1 * f);
+
+    double Fo[nc];
+#pragma unroll 1
+    for (int k = 0; k < nc; k++) {
+        double lrow[nc], rcol[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            double lv = Lm[0][c], rv = Rm[c][0];
+#pragma unroll
+            for (int kk = 1; kk < nc; kk++)
+                if (k == kk) { lv = Lm[kk][c]; rv = Rm[c][kk]; }
+            lrow[c] = lv;
+            rcol[c] = rv;
+        }
+        const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
+        double w[W], g[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            double wv = lrow[0] * SQ(SL::QU, fo + j, p);
+            double gv = lrow[0] * SQ(SL::QF, fo + j, p);
+#pragma unroll
+            for (int c = 1; c < nc; c++) {
+                wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
+                gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
+            }
+            w[j] = wv;
+            g[j] = gv;
+        }
+        double hsum = 0.0;
+#pragma unroll 1
+        for (int s = 0; s < 2; s++) {
+            // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
+            const double sa = s ? -alpha : alpha;
+            double v[W];
+#pragma unroll
+            for (int kk = 0; kk < W; kk++) {
+                const double wk = s ? w[W - 1 - kk] : w[kk];
+                const double gk = s ? g[W - 1 - kk] : g[kk];
+                v[kk] = 0.5 * fma(sa, wk, gk);
+            }
+            uint8_t fl;
+            const double val = teno_recon<H>(v, a.K, fl);
+            if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
+            hsum = s ? hsum + val : val;
+        }
+#pragma unroll
+        for (int c = 0; c < nc; c++) Fo[c] = (k == 0) ? rcol[c] * hsum : fma(rcol[c], hsum, Fo[c]);
+    }
+
+    if (a.K.limiter) {
+        // Positivity-preserving flux limiter (cited in Sec. 5.3): blend toward
+        // the Lax-Friedrichs flux so that the one-sided half updates of cells i
+        // and i+1 keep rho >= eps and p >= eps.
+        const double eps = a.K.lim_eps, lam2 = 2.0 * a.st->lam[D];
+        const double al = SQ(SL::QLR, jl, p), arr = SQ(SL::QLR, jr, p);
+        const double af = arr > al ? arr : al;
+        double FL[nc], dF[nc], UL[nc], UR[nc], dUL[nc], dUR[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            const double Ul = SQ(SL::QU + c, jl, p), Ur = SQ(SL::QU + c, jr, p);
+            const double Fl = SQ(SL::QF + c, jl, p), Fr = SQ(SL::QF + c, jr, p);
+            FL[c] = 0.5 * ((Fl + Fr) - af * (Ur - Ul));
+            dF[c] = Fo[c] - FL[c];
+            UL[c] = Ul - lam2 * (FL[c] - Fl);
+            UR[c] = Ur + lam2 * (FL[c] - Fr);
+            dUL[c] = -(lam2 * dF[c]);
+            dUR[c] = lam2 * dF[c];
+        }
+        double th = 1.0;
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const double r0 = side ? UR[0] : UL[0];
+            const double r1 = r0 + (side ? dUR[0] : dUL[0]);
+            if (r1 < eps) {
+                double t = (r0 - eps) / (r0 - r1);
+                if (!(t > 0.0)) t = 0.0;
+                if (t < th) th = t;
+            }
+        }
+        double thp = th;
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            double Us[nc], Ut[nc];
+#pragma unroll
+            for (int c = 0; c < nc; c++) {
+                Us[c] = side ? UR[c] : UL[c];
+                Ut[c] = Us[c] + th * (side ? dUR[c] : dUL[c]);
+            }
+            const double pt = pressure_of<ND>(Ut, a.K.gm1);
+            if (pt < eps) {
+                const double p0 = pressure_of<ND>(Us, a.K.gm1);
+                double t = th * ((p0 - eps) / (p0 - pt));
+                if (!(t > 0.0)) t = 0.0;
+                if (t < thp) thp = t;
+            }
+        }
+        if (thp < 1.0) {
+#pragma unroll
+            for (int c = 0; c < nc; c++) Fo[c] = FL[c] + thp * dF[c];
+        }
+    }
+
+#pragma unroll
+    for (int c = 0; c < nc; c++) a.F[c * a.nfaces + flin] = Fo[c];
+#undef SQ
+}
+
+// Host-side launch of one direction's sweep.
+template <int ND, int H, int D>
+cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
+{
+    constexpr int TP = (D == 0) ? 1 : 32;
+    constexpr int TF = (D == 0) ? 128 : 8;
+    constexpr size_t smem = face_smem_bytes<ND, H, TP, TF>();
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(face_kernel<ND, H, D, TP, TF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid;
+    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)a.n[1], (unsigned)a.n[2]);
+    else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((a.n[1] + 1 + TF - 1) / TF), (unsigned)a.n[2]);
+    else grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1], (unsigned)((a.n[2] + 1 + TF - 1) / TF));
+    face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace teno

@@ -387,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {
             "workload": "3D Euler 256^3 periodic on [0,2pi]^3, Taylor-Green Mach 0.5 + seeded "
-                        "k^-5/3 solenoidal field (10% rms), TENO%d-AA, LLF, CFL 0.4; step = "
+                        "k^-5/3 solenoidal field (10%% rms), TENO%d-AA, LLF, CFL 0.4; step = "
                         "device CFL reduction + SSP-RK3 step" % scheme,
             "scheme": scheme, "cells": cells, "parallelism": "independent problem per GPU",
             "l2": "state 671 MB > 129 MB L2 (no flush needed)"},

@@ -68,8 +68,9 @@ def params(ndim, n, dx, scheme=8, gamma=1.4, bc=BC_PERIODIC, bc_lo=None, bc_hi=N
     for a in range(3):
         p.n[a] = int(n[a])
         p.dx[a] = float(dx[a])
-    lo = bc_lo if bc_lo is not None else [bc] * 3
-    hi = bc_hi if bc_hi is not None else [bc] * 3
+    lo = list(bc_lo) if bc_lo is not None else [bc] * 3
+    hi = list(bc_hi) if bc_hi is not None else [bc] * 3
+    lo, hi = lo + [bc] * (3 - len(lo)), hi + [bc] * (3 - len(hi))
     for a in range(3):
         p.bc_lo[a], p.bc_hi[a] = int(lo[a]), int(hi[a])
     p.gamma, p.alpha1, p.alpha2, p.cr = gamma, alpha1, alpha2, cr

@@ -142,7 +142,7 @@ def tgv_3d(n: int = 256, seed: int = 3001, scheme: int = 10, gamma: float = 1.4,
     Ksafe = np.where(K2 > 0, K2, 1.0)
     div = (KX * comps[0] + KY * comps[1] + KZ * comps[2]) / Ksafe
     comps = [comps[0] - KX * div, comps[1] - KY * div, comps[2] - KZ * div]
-    pert = [np.fft.irfftn(c, s=(n, n, n)) for c in comps]
+    pert = [np.fft.irfftn(c, s=(n, n, n), axes=(0, 1, 2)) for c in comps]
     del comps, KX, KY, KZ, K, K2, Ksafe, div
     rms_tgv = math.sqrt(np.mean(u * u + v * v + w * w))
     rms_p = math.sqrt(np.mean(pert[0] ** 2 + pert[1] ** 2 + pert[2] ** 2))

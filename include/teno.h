@@ -132,6 +132,32 @@ int teno_status(void *ws, void *stream, int64_t *nonphysical);
 int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int nsteps,
                       double cfl, double *t_host, void *ws, size_t ws_bytes, void *stream);
 
+/* Size of the device array behind teno_rhs_static: 16 MiB. */
+#define TENO_RHS_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* teno_rhs without a workspace, for callers that cannot allocate device
+ * memory where they need a right-hand side (plugin code inside an
+ * application that owns the device memory pool, code with a memory budget
+ * fixed at start-up, code that must not call cudaMalloc while a CUDA graph
+ * is captured).  The paper has no counterpart; this is an integration aid.
+ *   Same arguments and result as teno_rhs, minus ws / ws_bytes.  Scratch is
+ *   one file-scope device array of TENO_RHS_STATIC_SCRATCH_BYTES, present on
+ *   every GPU where the library's kernels are loaded until the process exits.
+ *   Problems whose status header plus face-flux buffers (256 bytes + 8 *
+ *   ncons * sum over directions of the face-grid size, each part rounded up
+ *   to 256 bytes) exceed it are rejected with TENO_EINVAL before anything is
+ *   enqueued.  Allocates nothing (no cudaMalloc / cudaFree).
+ *   The first call on a device resolves the array's device address (one
+ *   cudaGetSymbolAddress with that device current); make that first call
+ *   before any stream capture.
+ *   All calls share the one array and each zeroes its status header: calls
+ *   whose work overlaps on the GPU (different streams, or different host
+ *   threads without ordering) race on it and must be serialised by the
+ *   caller.  The non-physical counter is not reported (teno_status needs a
+ *   workspace). */
+int teno_rhs_static(const teno_params *p, const double *U, double *rhs, double dt_limiter,
+                    uint8_t *flags, void *stream);
+
 /* Live timing of the dominant kernel (the face-sweep kernel) for roofline
  * reporting.  teno_profile_enable(1) clears the record and from then on
  * brackets every face-sweep launch with a pair of CUDA events recorded on

@@ -72,6 +72,7 @@ def load():
         lib.teno_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
         lib.teno_advance_host.argtypes = [P, vp, vp, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double), vp, sz, vp]
+        lib.teno_rhs_static.argtypes = [P, vp, vp, ctypes.c_double, vp, vp]
         lib.teno_profile_enable.argtypes = [ctypes.c_int]
         lib.teno_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64),
@@ -80,7 +81,7 @@ def load():
         lib.teno_strerror.restype = ctypes.c_char_p
         for name in ("teno_workspace_bytes", "teno_flags_bytes", "teno_rhs", "teno_rk3_step",
                      "teno_cfl_dt", "teno_status", "teno_advance_host", "teno_profile_enable",
-                     "teno_profile_read"):
+                     "teno_profile_read", "teno_rhs_static"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -88,7 +89,9 @@ def load():
 
 EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno_rhs",
            "teno_rk3_step", "teno_cfl_dt", "teno_status", "teno_advance_host",
-           "teno_profile_enable", "teno_profile_read", "teno_strerror")
+           "teno_profile_enable", "teno_profile_read", "teno_strerror", "teno_rhs_static")
+
+TENO_RHS_STATIC_SCRATCH_BYTES = 16 << 20
 
 
 # ---------------------------------------------------------------------------
@@ -155,6 +158,19 @@ def teno_flags_bytes(p: teno_params) -> int:
 def teno_rhs(p, U, rhs, dt_limiter=0.0, flags=None, ws=None, stream=None):
     _check(load().teno_rhs(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter), _ptr(flags),
                            _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "teno_rhs")
+
+
+def teno_rhs_static(p, U, rhs, dt_limiter=0.0, flags=None, stream=None):
+    """teno_rhs for callers that cannot allocate: scratch comes from the
+    library's fixed device array (TENO_RHS_STATIC_SCRATCH_BYTES).  Calls that
+    overlap on the GPU race on that array; serialise them."""
+    need = teno_workspace_bytes(p) - 8 * (p.ndim + 2) * p.n[0] * p.n[1] * p.n[2]
+    if need > TENO_RHS_STATIC_SCRATCH_BYTES + 256:
+        raise ValueError("teno_rhs_static: this grid needs about %d bytes of scratch but the "
+                         "static array holds %d; use teno_rhs with a workspace"
+                         % (need, TENO_RHS_STATIC_SCRATCH_BYTES))
+    _check(load().teno_rhs_static(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter),
+                                  _ptr(flags), _stream(stream)), "teno_rhs_static")
 
 
 def teno_rk3_step(p, U, dt=0.0, dt_device=None, ws=None, stream=None):

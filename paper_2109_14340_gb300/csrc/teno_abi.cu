@@ -3,6 +3,7 @@
 //   [wave maxima] -> prepare -> face sweep x [-> y [-> z]] -> combine.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "teno.h"
 #include "teno_face.cuh"
@@ -529,3 +530,59 @@ const char *teno_strerror(int code)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// teno_rhs_static: teno_rhs without a caller-supplied workspace.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// right-hand side -- plugin code inside a host application that owns the
+// device memory pool, code with a memory budget fixed at start-up, or code
+// that must not call cudaMalloc while a CUDA graph is being captured.  This
+// entry point takes its scratch (status header + face-flux buffers) from one
+// file-scope device array instead of a workspace; it calls no cudaMalloc,
+// cudaFree or other allocating routine.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_rhs_scratch[TENO_RHS_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+// Device address of g_rhs_scratch on the current device, resolved once per
+// device (the host-side symbol is only a stand-in, never a device address).
+static int rhs_scratch_address(void **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return TENO_EINVAL;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *ptr = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_rhs_scratch));
+        g_scratch_ptr[dev] = ptr;
+    }
+    *out = g_scratch_ptr[dev];
+    return TENO_OK;
+}
+
+extern "C" int teno_rhs_static(const teno_params *p, const double *U, double *rhs,
+                               double dt_limiter, uint8_t *flags, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(rhs) || U == rhs) return TENO_EINVAL;
+    if (p->limiter && !(dt_limiter >= 0.0)) return TENO_EINVAL;
+    // The right-hand side needs the status header and the face-flux buffers
+    // (the part of the workspace layout before the RK stage buffer).
+    if (layout(p).stage > (size_t)TENO_RHS_STATIC_SCRATCH_BYTES) return TENO_EINVAL;
+    void *scratch = nullptr;
+    if ((r = rhs_scratch_address(&scratch))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: zero the status header
+    // (counters and reduction slots) before use.
+    CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(Status), s));
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)scratch, s);
+}

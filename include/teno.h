@@ -132,6 +132,68 @@ int teno_status(void *ws, void *stream, int64_t *nonphysical);
 int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int nsteps,
                       double cfl, double *t_host, void *ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched mode: many independent 1D problems of uneven size advanced together.
+ * Each problem is a 1D Euler grid with its own size, spacing, scheme width,
+ * limiter switch and boundary rules, and its own CFL time step per step (the
+ * per-problem reduction of teno_cfl_dt).  The shared parameters (gamma, C_T
+ * parameters, flux splitting) come from a teno_params template with ndim 1.
+ * ------------------------------------------------------------------------ */
+typedef struct teno_batch_problem {
+    int64_t n;             /* cells (>= scheme/2)                               */
+    int64_t offset;        /* first double of this problem's state inside the
+                              packed array; its state there is [3][n] SoA
+                              (rho, rho*u, E); offsets 16-byte aligned, state
+                              blocks must not overlap                          */
+    double dx;             /* spacing (> 0)                                     */
+    int32_t scheme;        /* 8 or 10                                           */
+    int32_t limiter;       /* 0 or 1 (positivity-preserving limiter, Sec. 5.3) */
+    int32_t bc_lo, bc_hi;  /* TENO_BC_* at the two ends                         */
+} teno_batch_problem;
+
+typedef struct teno_batch teno_batch;   /* opaque host-side plan */
+
+/* How teno_batch_rk3_steps launches one step. */
+#define TENO_BATCH_GRAPH 0        /* persistent kernels over the (problem, tile)
+                                     work list, the step captured once in a CUDA
+                                     graph and replayed                         */
+#define TENO_BATCH_STREAM 1       /* the same persistent kernels, launched
+                                     directly                                   */
+#define TENO_BATCH_PER_PROBLEM 2  /* reference: teno_cfl_dt + teno_rk3_step for
+                                     each problem in turn                       */
+
+/* Build the plan (work lists, per-problem descriptors) on the host.  The plan
+ * owns host memory only (and, once a graph step runs, a CUDA graph and a
+ * capture stream); release it with teno_batch_destroy. */
+int teno_batch_create(const teno_params *common, const teno_batch_problem *probs,
+                      int32_t nprob, teno_batch **out);
+
+/* Device workspace bytes for this plan (status, per-problem slots, work lists,
+ * face-flux buffers, stage buffer, and the largest per-problem workspace of
+ * TENO_BATCH_PER_PROBLEM). */
+int teno_batch_workspace_bytes(const teno_batch *b, size_t *bytes);
+
+/* Autotuner: times one step (TENO_BATCH_STREAM) of every candidate tile width
+ * (64/128/256 faces, i.e. 2/4/8 warps per pencil tile) and persistent grid size
+ * (1/2/4 blocks per SM) on U_scratch (advanced in place: pass a copy) and keeps
+ * the fastest in the plan.  Results do not depend on the choice.
+ * *chosen_tile and *chosen_blocks_per_sm (nullable) report it. */
+int teno_batch_autotune(teno_batch *b, double *U_scratch, void *ws, size_t ws_bytes,
+                        void *stream, int32_t *chosen_tile, int32_t *chosen_blocks_per_sm);
+
+/* Advance every problem nsteps SSP-RK3 steps, each problem with its own
+ * dt = cfl / (A / dx) from its own state (Sec. 5), on the packed device state
+ * U.  mode: TENO_BATCH_GRAPH, TENO_BATCH_STREAM or TENO_BATCH_PER_PROBLEM; all
+ * three give bitwise identical states. */
+int teno_batch_rk3_steps(teno_batch *b, double *U, int32_t nsteps, double cfl, int32_t mode,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronise and copy each problem's accumulated time (sum of its dt since
+ * the workspace was first used by a persistent-mode step) to t_host[nprob]. */
+int teno_batch_times(const teno_batch *b, void *ws, void *stream, double *t_host);
+
+void teno_batch_destroy(teno_batch *b);
+
 /* Size of the device array behind teno_rhs_static: 16 MiB. */
 #define TENO_RHS_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -31,6 +31,16 @@ class TenoError(RuntimeError):
         self.code = code
 
 
+TENO_BATCH_GRAPH, TENO_BATCH_STREAM, TENO_BATCH_PER_PROBLEM = 0, 1, 2
+
+
+class teno_batch_problem(ctypes.Structure):
+    """Mirror of struct teno_batch_problem (include/teno.h)."""
+    _fields_ = [("n", ctypes.c_int64), ("offset", ctypes.c_int64), ("dx", ctypes.c_double),
+                ("scheme", ctypes.c_int32), ("limiter", ctypes.c_int32),
+                ("bc_lo", ctypes.c_int32), ("bc_hi", ctypes.c_int32)]
+
+
 class teno_params(ctypes.Structure):
     """Mirror of struct teno_params (include/teno.h)."""
     _fields_ = [
@@ -73,6 +83,16 @@ def load():
         lib.teno_advance_host.argtypes = [P, vp, vp, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double), vp, sz, vp]
         lib.teno_rhs_static.argtypes = [P, vp, vp, ctypes.c_double, vp, vp]
+        BP = ctypes.POINTER(teno_batch_problem)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.teno_batch_create.argtypes = [P, BP, ctypes.c_int32, ctypes.POINTER(vp)]
+        lib.teno_batch_workspace_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        lib.teno_batch_autotune.argtypes = [vp, vp, vp, sz, vp, i32p, i32p]
+        lib.teno_batch_rk3_steps.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_int32, vp, sz, vp]
+        lib.teno_batch_times.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.teno_batch_destroy.argtypes = [vp]
+        lib.teno_batch_destroy.restype = None
         lib.teno_profile_enable.argtypes = [ctypes.c_int]
         lib.teno_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64),
@@ -81,7 +101,9 @@ def load():
         lib.teno_strerror.restype = ctypes.c_char_p
         for name in ("teno_workspace_bytes", "teno_flags_bytes", "teno_rhs", "teno_rk3_step",
                      "teno_cfl_dt", "teno_status", "teno_advance_host", "teno_profile_enable",
-                     "teno_profile_read", "teno_rhs_static"):
+                     "teno_profile_read", "teno_rhs_static", "teno_batch_create",
+                     "teno_batch_workspace_bytes", "teno_batch_autotune", "teno_batch_rk3_steps",
+                     "teno_batch_times"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -89,7 +111,9 @@ def load():
 
 EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno_rhs",
            "teno_rk3_step", "teno_cfl_dt", "teno_status", "teno_advance_host",
-           "teno_profile_enable", "teno_profile_read", "teno_strerror", "teno_rhs_static")
+           "teno_profile_enable", "teno_profile_read", "teno_strerror", "teno_rhs_static",
+           "teno_batch_create", "teno_batch_workspace_bytes", "teno_batch_autotune",
+           "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy")
 
 TENO_RHS_STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -257,3 +281,93 @@ class Solver:
 
     def status(self, stream=None):
         return teno_status(self.ws, stream)
+
+
+# ---------------------------------------------------------------------------
+# batched mode
+# ---------------------------------------------------------------------------
+
+def pack_offsets(sizes):
+    """Offsets (in doubles, 16-byte aligned) of [3][n] state blocks packed
+    back to back, and the total length."""
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += 3 * int(n)
+        o += o & 1
+    return offs, o
+
+
+def teno_batch_create(common: teno_params, problems):
+    """problems: sequence of dicts with n, offset, dx, scheme, limiter,
+    bc_lo, bc_hi.  Returns an opaque handle (free with teno_batch_destroy)."""
+    arr = (teno_batch_problem * len(problems))()
+    for i, q in enumerate(problems):
+        arr[i].n, arr[i].offset, arr[i].dx = int(q["n"]), int(q["offset"]), float(q["dx"])
+        arr[i].scheme, arr[i].limiter = int(q["scheme"]), int(q.get("limiter", 0))
+        arr[i].bc_lo, arr[i].bc_hi = int(q.get("bc_lo", 1)), int(q.get("bc_hi", 1))
+    h = ctypes.c_void_p()
+    _check(load().teno_batch_create(ctypes.byref(common), arr, len(problems), ctypes.byref(h)),
+           "teno_batch_create")
+    return h
+
+
+def teno_batch_workspace_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(load().teno_batch_workspace_bytes(h, ctypes.byref(n)), "teno_batch_workspace_bytes")
+    return n.value
+
+
+def teno_batch_autotune(h, U_scratch, ws, stream=None):
+    t, bps = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().teno_batch_autotune(h, _ptr(U_scratch), _ptr(ws), ws.numel() * ws.element_size(),
+                                      _stream(stream), ctypes.byref(t), ctypes.byref(bps)),
+           "teno_batch_autotune")
+    return t.value, bps.value
+
+
+def teno_batch_rk3_steps(h, U, nsteps, cfl, mode, ws, stream=None):
+    _check(load().teno_batch_rk3_steps(h, _ptr(U), int(nsteps), float(cfl), int(mode), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_batch_rk3_steps")
+
+
+def teno_batch_times(h, ws, nprob, stream=None):
+    out = (ctypes.c_double * nprob)()
+    _check(load().teno_batch_times(h, _ptr(ws), _stream(stream), out), "teno_batch_times")
+    return list(out)
+
+
+def teno_batch_destroy(h):
+    if h:
+        load().teno_batch_destroy(h)
+
+
+class Batch:
+    """Owns a batch plan and its workspace."""
+
+    def __init__(self, common: teno_params, problems, device="cuda"):
+        import torch
+        self.problems = problems
+        self.h = teno_batch_create(common, problems)
+        nb = teno_batch_workspace_bytes(self.h)
+        # 256-byte aligned workspace
+        self._ws = torch.zeros((nb + 512) // 8, dtype=torch.float64, device=device)
+        shift = (-self._ws.data_ptr() % 256) // 8
+        self.ws = self._ws[shift:shift + (nb + 7) // 8]
+
+    def autotune(self, U_scratch, stream=None):
+        return teno_batch_autotune(self.h, U_scratch, self.ws, stream)
+
+    def steps(self, U, nsteps, cfl=0.4, mode=TENO_BATCH_GRAPH, stream=None):
+        teno_batch_rk3_steps(self.h, U, nsteps, cfl, mode, self.ws, stream)
+
+    def times(self, stream=None):
+        return teno_batch_times(self.h, self.ws, len(self.problems), stream)
+
+    def __del__(self):
+        try:
+            teno_batch_destroy(self.h)
+        except Exception:
+            pass
+        self.h = None

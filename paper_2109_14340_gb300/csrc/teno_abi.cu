@@ -327,6 +327,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.nfaces = face_grid(p, d);
         a.bc_lo = p->bc_lo[d];
         a.bc_hi = p->bc_hi[d];
+        a.lam = &st->lam[d];
         a.K = K;
         const int slot = (g_prof.on && g_prof.used < ProfileRecord::kMax) ? g_prof.used++ : -1;
         if (slot >= 0) {

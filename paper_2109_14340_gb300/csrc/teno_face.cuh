@@ -21,6 +21,7 @@ struct FaceArgs {
     int64_t n[3];
     int64_t ncell, nfaces;
     int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
+    const double *lam;     // limiter's effective dt/dx for this direction (device)
     Consts K;
 };
 
@@ -57,20 +58,20 @@ constexpr size_t face_smem_bytes()
     return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP;
 }
 
+// One tile: faces f0 .. f0+TF-1 along D of the TP pencils starting at x0
+// (at y, z for the axes not swept).  Every thread of the block calls it; it
+// synchronises once after staging and returns with no barrier pending, so a
+// persistent caller must synchronise before reusing the shared tile.
 template <int ND, int H, int D, int TP, int TF>
-__global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
+__device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_t x0, int64_t y,
+                                           int64_t z, double *sm)
 {
     using SL = SmemLayout<ND>;
     constexpr int nc = ND + 2, last = nc - 1, W = 2 * H;
     constexpr int NS = TF + 2 * H - 1;
-    extern __shared__ double sm[];
 #define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
 
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
-    int64_t x0 = 0, y = 0, z = 0, f0;
-    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = blockIdx.y; z = blockIdx.z; }
-    else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
-    else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
 
     // Stage cells f0-H .. f0+TF+H-2 along D.
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
     const int64_t f = f0 + fo;
     if (f > nD || (D != 0 && x0 + p >= n0)) return;
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
+    (void)last;
 
     // Roe average and eigenvectors (Sec. 5).
     double ul[ND], ur[ND];
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
         // Positivity-preserving flux limiter (cited in Sec. 5.3): blend toward
         // the Lax-Friedrichs flux so that the one-sided half updates of cells i
         // and i+1 keep rho >= eps and p >= eps.
-        const double eps = a.K.lim_eps, lam2 = 2.0 * a.st->lam[D];
+        const double eps = a.K.lim_eps, lam2 = 2.0 * (*a.lam);
         const double al = SQ(SL::QLR, jl, p), arr = SQ(SL::QLR, jr, p);
         const double af = arr > al ? arr : al;
         double FL[nc], dF[nc], UL[nc], UR[nc], dUL[nc], dUR[nc];
@@ -239,6 +241,17 @@ __global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
 #pragma unroll
     for (int c = 0; c < nc; c++) a.F[c * a.nfaces + flin] = Fo[c];
 #undef SQ
+}
+
+template <int ND, int H, int D, int TP, int TF>
+__global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
+{
+    extern __shared__ double sm[];
+    int64_t x0 = 0, y = 0, z = 0, f0;
+    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = blockIdx.y; z = blockIdx.z; }
+    else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
+    else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
+    face_block<ND, H, D, TP, TF>(a, f0, x0, y, z, sm);
 }
 
 // Host-side launch of one direction's sweep.

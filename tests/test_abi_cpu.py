@@ -74,3 +74,38 @@ def test_invalid_parameters(lib, bad):
 def test_strerror(lib):
     assert "invalid" in lib.teno_strerror(lib.TENO_EINVAL)
     assert lib.teno_strerror(99) == "unknown error code"
+
+
+def _probs(lib, sizes, schemes, offsets=None):
+    offs, _ = lib.pack_offsets(sizes)
+    offs = offsets or offs
+    return [dict(n=n, offset=o, dx=1.0 / n, scheme=s, limiter=0, bc_lo=1, bc_hi=1)
+            for n, s, o in zip(sizes, schemes, offs)]
+
+
+def test_batch_plan_host_logic(lib):
+    common = lib.teno_params_init()
+    h = lib.teno_batch_create(common, _probs(lib, [64, 100, 7], [8, 10, 8]))
+    try:
+        nb = lib.teno_batch_workspace_bytes(h)
+        faces = 65 + 101 + 8
+        assert nb > 8 * 3 * (faces + 64 + 100 + 7)
+    finally:
+        lib.teno_batch_destroy(h)
+
+
+@pytest.mark.parametrize("bad", ["overlap", "odd_offset", "too_small", "scheme"])
+def test_batch_plan_rejects(lib, bad):
+    common = lib.teno_params_init()
+    sizes, schemes, offs = [64, 64], [8, 10], None
+    if bad == "overlap":
+        offs = [0, 100]
+    elif bad == "odd_offset":
+        offs = [0, 193]
+    elif bad == "too_small":
+        sizes = [64, 4]
+    elif bad == "scheme":
+        schemes = [8, 9]
+    with pytest.raises(lib.TenoError) as e:
+        lib.teno_batch_create(common, _probs(lib, sizes, schemes, offs))
+    assert e.value.code == lib.TENO_EINVAL

@@ -84,14 +84,17 @@ void teno_params_init(teno_params *p);
  * Returns TENO_EINVAL for invalid parameters (then *bytes is untouched). */
 int teno_workspace_bytes(const teno_params *p, size_t *bytes);
 
-/* Bytes of the per-face decision record written by teno_rhs (flags != NULL):
- * for each direction d < ndim, for each face of the face grid (n with
- * n[d] + 1, x fastest), for each characteristic field k < ncons, for the
- * + then - split flux, one byte: bits 0-1 selected large stencil S_L as
+/* Bytes of the per-face decision record written by teno_rhs (flags != NULL).
+ * Part 1, for each direction d < ndim in turn, for each face of the face grid
+ * (n with n[d] + 1, x fastest), for each characteristic field k < ncons, for
+ * the + then - split flux, one byte: bits 0-1 selected large stencil S_L as
  * L - 2 (1: S3, 2: S4, 3: S5) or 0 for the small-stencil fallback of Eq.
  * renormalize; bits 2-4 the cut-offs delta_0..delta_2 of Eq. cutoff in the
  * fallback (else 0); bits 5-7 the C_T exponent [beta] of Eq. CT_definition
- * minus 7 (mod 8). */
+ * minus 7 (mod 8).  Part 2, for each direction in turn, for each face, one
+ * little-endian 16-bit word: the stencil cells (0 .. 2H-1, from cell i-H+1)
+ * where the splitting speeds are maximal (first maximum), 4 bits each for
+ * |u_d - c|, |u_d|, |u_d + c| and |u_d| + c. */
 int teno_flags_bytes(const teno_params *p, size_t *bytes);
 
 /* Semi-discrete right-hand side L(U) = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d
@@ -193,6 +196,53 @@ int teno_batch_rk3_steps(teno_batch *b, double *U, int32_t nsteps, double cfl, i
 int teno_batch_times(const teno_batch *b, void *ws, void *stream, double *t_host);
 
 void teno_batch_destroy(teno_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Adjoint (pattern: differentiation).  With the forward's discrete decisions
+ * frozen -- stencil selection and cut-offs per face, field and sign (the
+ * decision record of teno_flags_bytes), the cell maximising each splitting
+ * speed -- the TENO-AA reconstruction (Sec. 3.3) is a fixed linear scheme and
+ * L(U) is differentiable.  These calls apply the transposed Jacobian.  The
+ * positivity limiter is not differentiated: p->limiter must be 0.
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes for teno_rhs_vjp / teno_rk3_step_vjp (device, 256-byte
+ * aligned). */
+int teno_adjoint_workspace_bytes(const teno_params *p, size_t *bytes);
+
+/* mu = (dL/dU)^T lam at the state U (Eq. approximateEq differentiated).
+ *   U, lam, mu  device, ncons * ncells doubles; mu must not alias U or lam
+ *   flags       the decision record of L(U) (teno_rhs with flags), or NULL to
+ *               have it recomputed into the workspace first
+ * Deterministic: every cell gathers its contributions in a fixed order. */
+int teno_rhs_vjp(const teno_params *p, const double *U, const double *lam, const uint8_t *flags,
+                 double *mu, void *ws, size_t ws_bytes, void *stream);
+
+/* teno_rk3_step with the stages kept for the adjoint: U (in: U^n, out:
+ * U^{n+1}), U1 and U2 receive the first two stage states and flags (3 x
+ * teno_flags_bytes) the decision records of the three RHS evaluations.
+ * Bitwise the same U^{n+1} as teno_rk3_step with the host dt.  ws is a
+ * forward workspace (teno_workspace_bytes). */
+int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                         uint8_t *flags, void *ws, size_t ws_bytes, void *stream);
+
+/* The frozen-decision map whose derivative the adjoint applies: L(U) (and one
+ * SSP-RK3 step) with every reconstruction taken from the recorded decision
+ * bytes (one teno_flags_bytes block for teno_rhs_frozen; three, one per
+ * stage, for teno_rk3_step_frozen) instead of the smoothness indicators.
+ * With the decisions U itself produces, the result equals teno_rhs /
+ * teno_rk3_step up to rounding.  ws is a forward workspace. */
+int teno_rhs_frozen(const teno_params *p, const double *U, double *rhs, double dt_limiter,
+                    const uint8_t *decisions, void *ws, size_t ws_bytes, void *stream);
+int teno_rk3_step_frozen(const teno_params *p, double *U, double dt, const uint8_t *decisions,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Reverse of one SSP-RK3 step (Eq. Runge-kutta) at fixed dt: abar holds the
+ * adjoint of U^{n+1} on entry and that of U^n on return.  Un, U1, U2, flags as
+ * written by teno_rk3_step_record for that step. */
+int teno_rk3_step_vjp(const teno_params *p, const double *Un, const double *U1, const double *U2,
+                      const uint8_t *flags, double dt, double *abar, void *ws, size_t ws_bytes,
+                      void *stream);
 
 /* Size of the device array behind teno_rhs_static: 16 MiB. */
 #define TENO_RHS_STATIC_SCRATCH_BYTES (16u << 20)

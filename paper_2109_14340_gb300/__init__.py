@@ -83,6 +83,13 @@ def load():
         lib.teno_advance_host.argtypes = [P, vp, vp, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double), vp, sz, vp]
         lib.teno_rhs_static.argtypes = [P, vp, vp, ctypes.c_double, vp, vp]
+        u8p = ctypes.c_void_p
+        lib.teno_adjoint_workspace_bytes.argtypes = [P, ctypes.POINTER(sz)]
+        lib.teno_rhs_vjp.argtypes = [P, vp, vp, vp, vp, vp, sz, vp]
+        lib.teno_rk3_step_record.argtypes = [P, vp, ctypes.c_double, vp, vp, u8p, vp, sz, vp]
+        lib.teno_rk3_step_vjp.argtypes = [P, vp, vp, vp, u8p, ctypes.c_double, vp, vp, sz, vp]
+        lib.teno_rhs_frozen.argtypes = [P, vp, vp, ctypes.c_double, u8p, vp, sz, vp]
+        lib.teno_rk3_step_frozen.argtypes = [P, vp, ctypes.c_double, u8p, vp, sz, vp]
         BP = ctypes.POINTER(teno_batch_problem)
         i32p = ctypes.POINTER(ctypes.c_int32)
         lib.teno_batch_create.argtypes = [P, BP, ctypes.c_int32, ctypes.POINTER(vp)]
@@ -103,7 +110,9 @@ def load():
                      "teno_cfl_dt", "teno_status", "teno_advance_host", "teno_profile_enable",
                      "teno_profile_read", "teno_rhs_static", "teno_batch_create",
                      "teno_batch_workspace_bytes", "teno_batch_autotune", "teno_batch_rk3_steps",
-                     "teno_batch_times"):
+                     "teno_batch_times", "teno_adjoint_workspace_bytes", "teno_rhs_vjp",
+                     "teno_rk3_step_record", "teno_rk3_step_vjp", "teno_rhs_frozen",
+                     "teno_rk3_step_frozen"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -113,7 +122,9 @@ EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno
            "teno_rk3_step", "teno_cfl_dt", "teno_status", "teno_advance_host",
            "teno_profile_enable", "teno_profile_read", "teno_strerror", "teno_rhs_static",
            "teno_batch_create", "teno_batch_workspace_bytes", "teno_batch_autotune",
-           "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy")
+           "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy",
+           "teno_adjoint_workspace_bytes", "teno_rhs_vjp", "teno_rk3_step_record",
+           "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen")
 
 TENO_RHS_STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -371,3 +382,119 @@ class Batch:
         except Exception:
             pass
         self.h = None
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+
+def teno_adjoint_workspace_bytes(p) -> int:
+    n = ctypes.c_size_t()
+    _check(load().teno_adjoint_workspace_bytes(ctypes.byref(p), ctypes.byref(n)),
+           "teno_adjoint_workspace_bytes")
+    return n.value
+
+
+def aligned_workspace(nbytes, device):
+    """A zeroed float64 tensor view whose data pointer is 256-byte aligned."""
+    import torch
+    raw = torch.zeros((nbytes + 512) // 8, dtype=torch.float64, device=device)
+    shift = (-raw.data_ptr() % 256) // 8
+    return raw[shift:shift + (nbytes + 7) // 8]
+
+
+def teno_rhs_vjp(p, U, lam, mu, flags=None, ws=None, stream=None):
+    _check(load().teno_rhs_vjp(ctypes.byref(p), _ptr(U), _ptr(lam), _ptr(flags), _ptr(mu),
+                               _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_rhs_vjp")
+
+
+def teno_rk3_step_record(p, U, dt, U1, U2, flags, ws, stream=None):
+    _check(load().teno_rk3_step_record(ctypes.byref(p), _ptr(U), float(dt), _ptr(U1), _ptr(U2),
+                                       _ptr(flags), _ptr(ws), ws.numel() * ws.element_size(),
+                                       _stream(stream)), "teno_rk3_step_record")
+
+
+def teno_rhs_frozen(p, U, rhs, decisions, ws, dt_limiter=0.0, stream=None):
+    _check(load().teno_rhs_frozen(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter),
+                                  _ptr(decisions), _ptr(ws), ws.numel() * ws.element_size(),
+                                  _stream(stream)), "teno_rhs_frozen")
+
+
+def teno_rk3_step_frozen(p, U, dt, decisions, ws, stream=None):
+    _check(load().teno_rk3_step_frozen(ctypes.byref(p), _ptr(U), float(dt), _ptr(decisions),
+                                       _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_rk3_step_frozen")
+
+
+def teno_rk3_step_vjp(p, Un, U1, U2, flags, dt, abar, ws, stream=None):
+    _check(load().teno_rk3_step_vjp(ctypes.byref(p), _ptr(Un), _ptr(U1), _ptr(U2), _ptr(flags),
+                                    float(dt), _ptr(abar), _ptr(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_rk3_step_vjp")
+
+
+def _rollout_class():
+    import torch
+
+    class TenoRollout(torch.autograd.Function):
+        """nsteps SSP-RK3 steps at a fixed dt; the backward walks checkpoint
+        segments in reverse: recompute the segment's steps keeping stage
+        states and decision records, then apply teno_rk3_step_vjp step by
+        step (decisions frozen as in the forward)."""
+
+        @staticmethod
+        def forward(ctx, U0, p, dt, nsteps, every):
+            dev = U0.device
+            ws = aligned_workspace(teno_workspace_bytes(p), dev)
+            U = U0.detach().contiguous().clone()
+            ckpts = []
+            for k in range(nsteps):
+                if k % every == 0:
+                    ckpts.append(U.clone())
+                teno_rk3_step(p, U, float(dt), None, ws)
+            ctx.p, ctx.dt, ctx.nsteps, ctx.every = p, float(dt), nsteps, every
+            ctx.ckpts = ckpts
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            p, dt, nsteps, every = ctx.p, ctx.dt, ctx.nsteps, ctx.every
+            dev = gU.device
+            abar = gU.detach().contiguous().clone()
+            fws = aligned_workspace(teno_workspace_bytes(p), dev)
+            aws = aligned_workspace(teno_adjoint_workspace_bytes(p), dev)
+            flb = teno_flags_bytes(p)
+            nseg = len(ctx.ckpts)
+            for s in reversed(range(nseg)):
+                start = s * every
+                stop = min(start + every, nsteps)
+                U = ctx.ckpts[s].clone()
+                rec = []
+                for _ in range(start, stop):
+                    Un = U.clone()
+                    U1 = torch.empty_like(U)
+                    U2 = torch.empty_like(U)
+                    fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
+                    teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
+                    rec.append((Un, U1, U2, fl))
+                for Un, U1, U2, fl in reversed(rec):
+                    teno_rk3_step_vjp(p, Un, U1, U2, fl, dt, abar, aws)
+                del rec
+            ctx.ckpts = None
+            return abar, None, None, None, None
+
+    return TenoRollout
+
+
+_ROLLOUT = None
+
+
+def rollout(p, U0, dt, nsteps, checkpoint_every=20):
+    """Differentiable: U(T) after nsteps SSP-RK3 steps of fixed dt from U0
+    (a CUDA float64 tensor [ncons, ncells]); gradients flow to U0 through
+    the frozen-decision adjoint with checkpoint-every-m recomputation."""
+    global _ROLLOUT
+    if _ROLLOUT is None:
+        _ROLLOUT = _rollout_class()
+    return _ROLLOUT.apply(U0, p, float(dt), int(nsteps), int(checkpoint_every))

@@ -305,7 +305,8 @@ static cudaError_t profile_mark(int which, int slot, cudaStream_t s)
 
 // One right-hand-side evaluation of Uk into the face buffers, then combine.
 static int stage(const teno_params *p, const double *Uk, const double *Un, double *out, int mode,
-                 double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s)
+                 double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s,
+                 const uint8_t *frozen = nullptr)
 {
     const Layout L = layout(p);
     Status *st = (Status *)(ws + L.status);
@@ -316,11 +317,21 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     prepare_kernel<<<1, 1, 0, s>>>(st, nd, dt_host, dt_dev, idx, p->limiter);
     CUDA_TRY(cudaGetLastError());
     uint8_t *fl = flags;
+    const uint8_t *fz = frozen;
+    // the decision record: all directions' decision bytes, then all
+    // directions' maximising-cell words
+    size_t dec_bytes = 0;
+    for (int d = 0; d < nd; d++) dec_bytes += (size_t)face_grid(p, d) * nc * 2;
+    uint16_t *am = flags ? (uint16_t *)(flags + dec_bytes) : nullptr;
+    const uint16_t *fam = frozen ? (const uint16_t *)(frozen + dec_bytes) : nullptr;
     for (int d = 0; d < nd; d++) {
         FaceArgs a;
         a.U = Uk;
         a.F = (double *)(ws + L.flux[d]);
         a.flags = fl;
+        a.frozen = fz;
+        a.argmax = am;
+        a.frozen_argmax = fam;
         a.st = st;
         for (int k = 0; k < 3; k++) a.n[k] = p->n[k];
         a.ncell = ncells(p);
@@ -338,6 +349,9 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         if (e != cudaSuccess) return TENO_ECUDA;
         if (slot >= 0) CUDA_TRY(profile_mark(1, slot, s));
         if (fl) fl += (size_t)face_grid(p, d) * nc * 2;
+        if (fz) fz += (size_t)face_grid(p, d) * nc * 2;
+        if (am) am += face_grid(p, d);
+        if (fam) fam += face_grid(p, d);
     }
     CombineArgs c;
     for (int d = 0; d < 3; d++) {
@@ -404,7 +418,7 @@ int teno_flags_bytes(const teno_params *p, size_t *bytes)
     if (r) return r;
     if (!bytes) return TENO_EINVAL;
     size_t t = 0;
-    for (int d = 0; d < p->ndim; d++) t += (size_t)face_grid(p, d) * ncons(p) * 2;
+    for (int d = 0; d < p->ndim; d++) t += (size_t)face_grid(p, d) * (ncons(p) * 2 + 2);
     *bytes = t;
     return TENO_OK;
 }
@@ -436,6 +450,51 @@ int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_d
     if ((r = stage(p, U, U, Us, 1, dt, dt_device, nullptr, (char *)ws, s))) return r;
     if ((r = stage(p, Us, U, Us, 2, dt, dt_device, nullptr, (char *)ws, s))) return r;
     return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s);
+}
+
+int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                         uint8_t *flags, void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(U1) || check_ptr(U2) || check_ptr(ws) || !flags) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total || !(dt >= 0.0)) return TENO_EINVAL;
+    size_t flb = 0;
+    teno_flags_bytes(p, &flb);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the stages of teno_rk3_step, with the stage states and decision records kept
+    if ((r = stage(p, U, U, U1, 1, dt, nullptr, flags, (char *)ws, s))) return r;
+    if ((r = stage(p, U1, U, U2, 2, dt, nullptr, flags + flb, (char *)ws, s))) return r;
+    return stage(p, U2, U, U, 3, dt, nullptr, flags + 2 * flb, (char *)ws, s);
+}
+
+int teno_rhs_frozen(const teno_params *p, const double *U, double *rhs, double dt_limiter,
+                    const uint8_t *decisions, void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(rhs) || check_ptr(ws) || !decisions || U == rhs) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total) return TENO_EINVAL;
+    if (p->limiter && !(dt_limiter >= 0.0)) return TENO_EINVAL;
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, nullptr, (char *)ws, (cudaStream_t)stream,
+                 decisions);
+}
+
+int teno_rk3_step_frozen(const teno_params *p, double *U, double dt, const uint8_t *decisions,
+                         void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(ws) || !decisions) return TENO_EINVAL;
+    if (ws_bytes < layout(p).total || !(dt >= 0.0)) return TENO_EINVAL;
+    size_t flb = 0;
+    teno_flags_bytes(p, &flb);
+    const Layout L = layout(p);
+    double *Us = (double *)((char *)ws + L.stage);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = stage(p, U, U, Us, 1, dt, nullptr, nullptr, (char *)ws, s, decisions))) return r;
+    if ((r = stage(p, Us, U, Us, 2, dt, nullptr, nullptr, (char *)ws, s, decisions + flb))) return r;
+    return stage(p, Us, U, U, 3, dt, nullptr, nullptr, (char *)ws, s, decisions + 2 * flb);
 }
 
 int teno_cfl_dt(const teno_params *p, const double *U, double cfl, double *dt_device,

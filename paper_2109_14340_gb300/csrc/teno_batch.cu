@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(TF) batch_face_kernel(
         a.U = U + d.u_off;
         a.F = F + d.f_off;
         a.flags = nullptr;
+        a.frozen = nullptr;
+        a.argmax = nullptr;
+        a.frozen_argmax = nullptr;
         a.st = st;
         a.n[0] = d.n; a.n[1] = 1; a.n[2] = 1;
         a.ncell = d.n;

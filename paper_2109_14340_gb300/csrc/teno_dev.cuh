@@ -200,6 +200,43 @@ __device__ __forceinline__ double teno_recon(const double (&v)[2 * H], const Con
 #undef V
 }
 
+// Frozen reconstruction coefficient of value index m (offset m - H + 1) for a
+// decision byte: the selected large stencil's linear scheme, or the
+// renormalised small-stencil blend.
+template <int H>
+__device__ __forceinline__ double frozen_coef(uint8_t flag, int m)
+{
+    const int sel = flag & 3;
+    const int off = m - H + 1;
+    if (sel == 3) return (off >= -4 && off <= 5) ? TENO_LIN5[off + 4] : 0.0;
+    if (sel == 2) return (off >= -3 && off <= 4) ? TENO_LIN4[off + 3] : 0.0;
+    if (sel == 1) return (off >= -2 && off <= 3) ? TENO_LIN3[off + 2] : 0.0;
+    const double dd0 = (flag & 4) ? TENO_DK[0] : 0.0;
+    const double dd1 = (flag & 8) ? TENO_DK[1] : 0.0;
+    const double dd2 = (flag & 16) ? TENO_DK[2] : 0.0;
+    const double den = (dd0 + dd1) + dd2;
+    const double w0 = dd0 / den, w1 = dd1 / den, w2 = dd2 / den;
+    switch (off) {
+    case -2: return 2.0 * w2 / 6.0;
+    case -1: return (-w0 - 7.0 * w2) / 6.0;
+    case 0: return (5.0 * w0 + 2.0 * w1 + 11.0 * w2) / 6.0;
+    case 1: return (2.0 * w0 + 5.0 * w1) / 6.0;
+    case 2: return -w1 / 6.0;
+    default: return 0.0;
+    }
+}
+
+// Reconstruction with a recorded decision: the same selection as the byte
+// says, applied as a fixed linear scheme (no smoothness indicators).
+template <int H>
+__device__ __forceinline__ double frozen_recon(const double (&v)[2 * H], uint8_t flag)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < 2 * H; m++) acc = fma(frozen_coef<H>(flag, m), v[m], acc);
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // Euler: primitive variables and physical flux of one cell (Eq. Euler, EOS).
 // ---------------------------------------------------------------------------

@@ -17,6 +17,10 @@ struct FaceArgs {
     const double *U;       // state, [nc][ncell]
     double *F;             // face fluxes of direction D, [nc][nfaces]
     uint8_t *flags;        // decision record of direction D or nullptr
+    const uint8_t *frozen; // recorded decisions to apply instead of deciding, or nullptr
+    uint16_t *argmax;      // per face: the maximising stencil cells of the splitting
+                           // speeds (4 bits each: u-c, u, u+c, |u|+c), or nullptr
+    const uint16_t *frozen_argmax;   // recorded maximising cells to apply, or nullptr
     Status *st;
     int64_t n[3];
     int64_t ncell, nfaces;
@@ -120,22 +124,32 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                                              SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
     if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
 
-    // Splitting speeds over the stencil.
-    double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
-#pragma unroll
-    for (int j = 0; j < W; j++) {
-        const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
-        const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
-        if (j == 0 || em > am) am = em;
-        if (j == 0 || e0 > a0) a0 = e0;
-        if (j == 0 || ep > ap) ap = ep;
-        if (j == 0 || er > ar) ar = er;
-    }
-
     int64_t flin;
     if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
     else if (D == 1) flin = x0 + p + n0 * (f + (n1 + 1) * z);
     else flin = x0 + p + n0 * (y + n1 * f);
+
+    // Splitting speeds over the stencil (first maximum), or at recorded cells.
+    double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
+    if (a.frozen_argmax) {
+        const unsigned w = a.frozen_argmax[flin];
+        am = SQ(SL::QLM, fo + (int)(w & 15), p);
+        a0 = SQ(SL::QL0, fo + (int)((w >> 4) & 15), p);
+        ap = SQ(SL::QLP, fo + (int)((w >> 8) & 15), p);
+        ar = SQ(SL::QLR, fo + (int)((w >> 12) & 15), p);
+    } else {
+        int jm = 0, j0 = 0, jp = 0, jr_ = 0;
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
+            const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
+            if (j == 0 || em > am) { am = em; jm = j; }
+            if (j == 0 || e0 > a0) { a0 = e0; j0 = j; }
+            if (j == 0 || ep > ap) { ap = ep; jp = j; }
+            if (j == 0 || er > ar) { ar = er; jr_ = j; }
+        }
+        if (a.argmax) a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
+    }
 
     double Fo[nc];
 #pragma unroll 1
@@ -177,7 +191,13 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 v[kk] = 0.5 * fma(sa, wk, gk);
             }
             uint8_t fl;
-            const double val = teno_recon<H>(v, a.K, fl);
+            double val;
+            if (a.frozen) {
+                fl = a.frozen[(flin * nc + k) * 2 + s];
+                val = frozen_recon<H>(v, fl);
+            } else {
+                val = teno_recon<H>(v, a.K, fl);
+            }
             if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
             hsum = s ? hsum + val : val;
         }

@@ -186,3 +186,75 @@ def batched_1d(count: int = 4096, seed: int = 4001, nmin: int = 64, nmax: int = 
         probs.append(_case(U, 1, [N], [1.0 / N], [TRANSMISSIVE], [TRANSMISSIVE], scheme, gamma,
                            limiter=1 if vac else 0))
     return probs
+
+
+def smooth_field(shape, seed, modes=4, amp=1.0, periodic_axes=None):
+    """Seeded smooth field on the unit box (sum of a few low Fourier modes),
+    shape (nz, ny, nx) or shorter; used for perturbations and directions."""
+    g = rng(seed)
+    grids = np.meshgrid(*[(np.arange(s) + 0.5) / s for s in shape], indexing="ij")
+    out = np.zeros(shape)
+    for _ in range(modes):
+        k = g.integers(1, 4, len(shape))
+        ph = g.uniform(0, 2 * np.pi)
+        a = g.uniform(-1, 1)
+        arg = sum(2 * np.pi * k[i] * grids[i] for i in range(len(shape))) + ph
+        out += a * np.sin(arg)
+    return amp * out / max(1e-300, np.abs(out).max())
+
+
+def adjoint_2d(n: int = 512, ny: int | None = None, seed: int = 5001, scheme: int = 8,
+               gamma: float = 1.4, target_seed: int = 5002, target_amp: float = 1e-3):
+    """Stationary Mach-2 normal shock at x = 0.5 on the unit square with a
+    uniform tangential velocity v = u1/2 (an oblique-shock flow that stays
+    y-periodic), upstream rho = 1, p = 1/gamma (c = 1), Rankine-Hugoniot
+    downstream; seeded smooth entropy wave + isentropic vortex upstream and a
+    1e-3 generic smooth field everywhere.
+    Transmissive in x, periodic in y.  Also returns the initial state of the
+    target run: the same IC plus a seeded smooth perturbation of relative
+    size target_amp."""
+    ny = n if ny is None else ny
+    g = rng(seed)
+    M = 2.0
+    r1, p1, u1 = 1.0, 1.0 / gamma, 2.0
+    r2 = r1 * (gamma + 1) * M * M / ((gamma - 1) * M * M + 2)
+    p2 = p1 * (1 + 2 * gamma / (gamma + 1) * (M * M - 1))
+    u2 = u1 * r1 / r2
+    vt = 0.5 * u1
+    x = (np.arange(n) + 0.5) / n
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    up = X < 0.5
+    rho = np.where(up, r1, r2)
+    u = np.where(up, u1, u2)
+    p = np.where(up, p1, p2)
+    win = 0.5 * (1 - np.tanh((X - 0.38) / 0.02))
+    ky = int(g.integers(1, 4))
+    kx = g.uniform(2, 6)
+    ph = g.uniform(0, 2 * np.pi)
+    rho = rho * (1 + 0.05 * win * np.sin(2 * np.pi * (kx * X + ky * Y) + ph))
+    x0, y0 = g.uniform(0.15, 0.3), g.uniform(0.3, 0.7)
+    eps, R = 0.3, 0.05
+    r2v = ((X - x0) ** 2 + (Y - y0) ** 2) / (R * R)
+    e = np.exp(0.5 * (1 - r2v))
+    u = u + eps / (2 * np.pi) * (-(Y - y0) / R) * e * win
+    v = vt + eps / (2 * np.pi) * ((X - x0) / R) * e * win
+    T1 = p1 / r1
+    dT = -(gamma - 1) * eps * eps / (8 * gamma * np.pi ** 2) * e * e * win
+    T = np.where(up, T1 + dT, p / rho)
+    rho = np.where(up, rho * ((T1 + dT) / T1) ** (1 / (gamma - 1)), rho)
+    p = np.where(up, rho * T, p)
+    # a small generic smooth field in every primitive variable, so that no
+    # characteristic field is constant only up to rounding (there TENO's
+    # decisions follow rounding noise and the map is not differentiable)
+    gen = smooth_field((4, ny, n), seed + 100, modes=6)
+    rho = rho * (1 + 1e-3 * gen[0])
+    u = u + 1e-3 * gen[1]
+    v = v + 1e-3 * gen[2]
+    p = p * (1 + 1e-3 * gen[3])
+    U = prim_to_cons(rho, [u, v], p, gamma)
+    pert = smooth_field((4, ny, n), target_seed)
+    Ut = U * (1 + target_amp * pert.reshape(4, -1))
+    return _case(U, 2, [n, ny], [1.0 / n, 1.0 / ny], [TRANSMISSIVE, PERIODIC],
+                 [TRANSMISSIVE, PERIODIC], scheme, gamma, U_target_ic=Ut, steps=200,
+                 checkpoint_every=20)

@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=512)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -306,6 +309,86 @@ def run_batched(args, dev, stream):
             "mode": "persistent (problem, tile) work list, step captured in a CUDA graph"}
 
 
+def run_adjoint(args, dev, stream):
+    """2D 512^2 TENO8-AA, Mach-2 oblique-shock flow with seeded entropy /
+    vortex perturbations, 200 RK3 steps at the dt of the initial state,
+    checkpoints every 20; loss = 1/2 ||rho(T) - rho_target||^2 with the
+    target from a seeded 1e-3 perturbation of the initial state.  Reports
+    backward (incl. recompute) / forward time and central differences of the
+    frozen-decision map along seeded directions against the gradient."""
+    import torch
+
+    import paper_2109_14340_gb300 as T
+    import workloads
+    n, nsteps, every = args.adjoint_n, args.adjoint_steps, 20
+    c = workloads.adjoint_2d(n)
+    p = T.teno_params_init(ndim=2, n=c["n"], dx=c["dx"], scheme=8, bc_lo=c["bc_lo"],
+                           bc_hi=c["bc_hi"])
+    s = T.Solver(p, dev)
+    U0 = torch.from_numpy(c["U"]).to(dev)
+    dt = float(s.cfl_dt(U0, 0.4).item())
+    rho_t = T.rollout(p, torch.from_numpy(c["U_target_ic"]).to(dev), dt, nsteps, every)[0].detach()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # warm-up (module load) on a short horizon
+    Uw = U0.clone().requires_grad_(True)
+    (0.5 * ((T.rollout(p, Uw, dt, 2, 1)[0] - rho_t) ** 2).sum()).backward()
+    torch.cuda.synchronize(dev)
+    U0g = U0.clone().requires_grad_(True)
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(stream)
+    UT = T.rollout(p, U0g, dt, nsteps, every)
+    loss = 0.5 * ((UT[0] - rho_t) ** 2).sum()
+    e1.record(stream)
+    loss.backward()
+    e2.record(stream)
+    torch.cuda.synchronize(dev)
+    t_f = e0.elapsed_time(e1) * 1e-3
+    t_b = e1.elapsed_time(e2) * 1e-3
+    grad = U0g.grad
+    # the recompute share: the same number of recorded steps on their own
+    fws = T.aligned_workspace(T.teno_workspace_bytes(p), dev)
+    flb = T.teno_flags_bytes(p)
+    U = U0.clone()
+    fls = []
+    e3, e4 = ev(), ev()
+    e3.record(stream)
+    for _ in range(nsteps):
+        U1, U2 = torch.empty_like(U), torch.empty_like(U)
+        fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
+        T.teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
+        fls.append(fl)
+        del U1, U2
+    e4.record(stream)
+    torch.cuda.synchronize(dev)
+    t_rec = e3.elapsed_time(e4) * 1e-3
+
+    def frozen(Ustart):
+        Uf = Ustart.clone()
+        for fl in fls:
+            T.teno_rk3_step_frozen(p, Uf, dt, fl, fws)
+        return 0.5 * float(((Uf[0] - rho_t) ** 2).sum())
+
+    scale = U0.abs().amax(dim=1, keepdim=True)
+    errs = []
+    for seed in (5003, 5004):
+        v = torch.from_numpy(workloads.smooth_field((4, n, n), seed).reshape(4, -1)).to(dev) * scale
+        h = 1e-6
+        fd = (frozen(U0 + h * v) - frozen(U0 - h * v)) / (2 * h)
+        ad = float((grad * v).sum())
+        errs.append(abs(fd - ad) / abs(ad))
+    del fls
+    return {"workload": "2D Euler %dx%d TENO8-AA, Mach-2 oblique shock + entropy/vortex, "
+                        "transmissive x / periodic y, %d steps at fixed dt, checkpoints every %d"
+                        % (n, n, nsteps, every),
+            "forward_s": t_f, "backward_s": t_b, "cost_ratio": t_b / t_f,
+            "cost_ratio_excluding_recompute": (t_b - t_rec) / t_f,
+            "fd_frozen_decisions_max_rel_err": max(errs), "fd_directions": len(errs),
+            "loss": float(loss)}
+
+
 def read_traffic_per_face(scheme):
     """Measured DRAM bytes per face of the face sweep, from the committed ncu
     summary (a line 'traffic_bytes_per_face[TENO<s>]: <value>')."""
@@ -434,6 +517,9 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, stream)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(args, dev, stream)
 
     if rank != 0:
         if dist is not None:
@@ -479,6 +565,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "cpu_baseline": cpu,
         "batched": batched,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -270,6 +270,26 @@ int teno_rk3_step_vjp(const teno_params *p, const double *Un, const double *U1, 
 int teno_rhs_static(const teno_params *p, const double *U, double *rhs, double dt_limiter,
                     uint8_t *flags, void *stream);
 
+/* The scalar TENO-AA reconstruction at face i+1/2 (Sec. 3.2-3.4, Sec. 4.2 and
+ * 4.3) of caller-provided stencils, e.g. split characteristic fluxes:
+ *   v      device, count * scheme doubles; stencil i holds v[i*scheme + m] at
+ *          offset m - scheme/2 + 1 from the upwind cell (m = 0 .. scheme-1)
+ *   out    device, count doubles: the reconstructed face values
+ *   flags  device, count bytes (nullable): the decision byte of each stencil
+ *          (layout of teno_flags_bytes part 1)
+ * Uses p->scheme and the C_T / epsilon parameters only. */
+int teno_reconstruct(const teno_params *p, const double *v, int64_t count, double *out,
+                     uint8_t *flags, void *stream);
+
+/* Process-wide switch of the certified decision filter (default on): 1 lets
+ * the face kernels decide the common case "largest stencil accepted" in
+ * single precision with rigorous error bounds, falling back to the full FP64
+ * evaluation whenever the bounds leave the decision open; 0 always evaluates
+ * the decisions in FP64.  Results are identical either way (the filter only
+ * answers when its answer equals the FP64 one); the switch exists to test
+ * and time that.  Not thread-safe with concurrent launches. */
+int teno_set_decision_filter(int on);
+
 /* Live timing of the dominant kernel (the face-sweep kernel) for roofline
  * reporting.  teno_profile_enable(1) clears the record and from then on
  * brackets every face-sweep launch with a pair of CUDA events recorded on

@@ -101,6 +101,8 @@ def load():
         lib.teno_batch_destroy.argtypes = [vp]
         lib.teno_batch_destroy.restype = None
         lib.teno_profile_enable.argtypes = [ctypes.c_int]
+        lib.teno_set_decision_filter.argtypes = [ctypes.c_int]
+        lib.teno_reconstruct.argtypes = [P, vp, ctypes.c_int64, vp, vp, vp]
         lib.teno_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]
@@ -108,7 +110,7 @@ def load():
         lib.teno_strerror.restype = ctypes.c_char_p
         for name in ("teno_workspace_bytes", "teno_flags_bytes", "teno_rhs", "teno_rk3_step",
                      "teno_cfl_dt", "teno_status", "teno_advance_host", "teno_profile_enable",
-                     "teno_profile_read", "teno_rhs_static", "teno_batch_create",
+                     "teno_profile_read", "teno_set_decision_filter", "teno_reconstruct", "teno_rhs_static", "teno_batch_create",
                      "teno_batch_workspace_bytes", "teno_batch_autotune", "teno_batch_rk3_steps",
                      "teno_batch_times", "teno_adjoint_workspace_bytes", "teno_rhs_vjp",
                      "teno_rk3_step_record", "teno_rk3_step_vjp", "teno_rhs_frozen",
@@ -121,6 +123,7 @@ def load():
 EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno_rhs",
            "teno_rk3_step", "teno_cfl_dt", "teno_status", "teno_advance_host",
            "teno_profile_enable", "teno_profile_read", "teno_strerror", "teno_rhs_static",
+           "teno_set_decision_filter", "teno_reconstruct",
            "teno_batch_create", "teno_batch_workspace_bytes", "teno_batch_autotune",
            "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy",
            "teno_adjoint_workspace_bytes", "teno_rhs_vjp", "teno_rk3_step_record",
@@ -237,6 +240,16 @@ def teno_advance_host(p, U_host, U_dev, nsteps, cfl, ws, stream=None):
                                     _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "teno_advance_host")
     return t.value
+
+
+def teno_reconstruct(p, v, out, flags=None, stream=None):
+    """v: CUDA float64 [count, scheme]; out: [count]; flags: uint8 [count]."""
+    _check(load().teno_reconstruct(ctypes.byref(p), _ptr(v), v.shape[0], _ptr(out), _ptr(flags),
+                                   _stream(stream)), "teno_reconstruct")
+
+
+def teno_set_decision_filter(on: bool = True):
+    _check(load().teno_set_decision_filter(1 if on else 0), "teno_set_decision_filter")
 
 
 def teno_profile_enable(on: bool = True):

@@ -81,17 +81,57 @@ def table(spec):
     return w, M
 
 
+def sym_norms(M, lo, w):
+    """Spectral norms of the symmetric matrix A (beta = s^T A s) of an upper-
+    triangular form M on the shifted values (offset 0 removed, since its
+    shifted value is zero), and of |A|; rounded up by 1 %."""
+    import numpy as np
+    idx = [r for r in range(w) if r + lo != 0]
+    A = np.zeros((len(idx), len(idx)))
+    for a, r in enumerate(idx):
+        for b, c in enumerate(idx):
+            if r == c:
+                A[a, b] = M[r][r]
+            elif r < c:
+                A[a, b] = A[b, a] = M[r][c] / 2.0
+    n1 = float(np.max(np.abs(np.linalg.eigvalsh(A))))
+    n2 = float(np.max(np.abs(np.linalg.eigvalsh(np.abs(A)))))
+    return n1 * 1.01, n2 * 1.01
+
+
 def emit():
+    import numpy as np
     out = ["// Generated by gen_coeffs.py from the integers of Eq. TENO10_AA",
            "// (arXiv 2109.14340, Sec. 4.2); do not edit.",
            "#pragma once", ""]
+    norms = {}
     for name, spec in (("TENO_Q6", W6), ("TENO_Q8", W8), ("TENO_Q10", W10)):
         w, M = table(spec)
         out.append("static __constant__ double %s[%d][%d] = {" % (name, w, w))
         for r in range(w):
             out.append("    {" + ", ".join(float(v).hex() if v else "0.0" for v in M[r]) + "},")
         out.append("};")
+        out.append("static __constant__ float %sF[%d][%d] = {" % (name, w, w))
+        for r in range(w):
+            out.append("    {" + ", ".join((float(np.float32(v)).hex() + "f") if v else "0.0f"
+                                           for v in M[r]) + "},")
+        out.append("};")
         out.append("")
+        norms[w] = sym_norms(M, spec[1], w)
+    # small indicators in shifted values: beta0 on (s-1, s1), beta1 on (s1, s2),
+    # beta2 on (s-2, s-1)
+    small = [np.array([[4 / 3, 5 / 6], [5 / 6, 4 / 3]]),
+             np.array([[25 / 3, -19 / 6], [-19 / 6, 4 / 3]]),
+             np.array([[4 / 3, -19 / 6], [-19 / 6, 25 / 3]])]
+    sn = [(float(np.max(np.abs(np.linalg.eigvalsh(A)))) * 1.01,
+           float(np.max(np.abs(np.linalg.eigvalsh(np.abs(A))))) * 1.01) for A in small]
+    out.append("// Spectral norms (||A||, || |A| ||, rounded up) of the indicator forms on")
+    out.append("// shifted values: small stencils S0, S1, S2, then S3, S4, S5.")
+    vals = sn + [norms[6], norms[8], norms[10]]
+    out.append("static __constant__ float TENO_BNORM[6][2] = {" +
+               ", ".join("{%r, %r}" % (float(np.float32(a)), float(np.float32(b))) for a, b in vals)
+               .replace("'", "") + "};")
+    out.append("")
     return "\n".join(out)
 
 

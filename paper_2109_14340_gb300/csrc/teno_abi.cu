@@ -1,6 +1,7 @@
 // C ABI of the TENO-AA library (declared in include/teno.h): parameter
 // validation, workspace layout, and the per-stage launch sequence
 //   [wave maxima] -> prepare -> face sweep x [-> y [-> z]] -> combine.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -158,6 +159,29 @@ __global__ void prepare_kernel(Status *st, int nd, double dt_host, const double 
     for (int d = 0; d < nd; d++) st->lam[d] = (dt * S) / A[d];
 }
 
+// Scalar reconstruction of caller-provided stencils (teno_reconstruct): the
+// certified filter first when enabled, else / then the exact path.
+template <int H>
+__global__ void recon_kernel(const double *v, int64_t count, double *out, uint8_t *flags, Consts K,
+                             FastK FK, int fast)
+{
+    constexpr int W = 2 * H;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double vv[W], sh[W];
+#pragma unroll
+        for (int m = 0; m < W; m++) vv[m] = v[i * W + m];
+#pragma unroll
+        for (int m = 0; m < W; m++) sh[m] = vv[m] - vv[H - 1];
+        uint8_t fl = 0;
+        double r;
+        if (fast && fast_accept<H>(vv, sh, beta_large_s<H, H>(sh), FK, fl)) r = flux_large<H, H>(vv);
+        else r = teno_recon<H>(vv, K, fl);
+        out[i] = r;
+        if (flags) flags[i] = fl;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -247,6 +271,13 @@ static Consts consts_of(const teno_params *p)
     K.split = p->flux_split;
     K.limiter = p->limiter;
     return K;
+}
+
+int g_fast_filter = 1;
+
+static FastK fastk_of(const teno_params *p)
+{
+    return fastk_make(p->ct_cr, p->ct_alpha1, p->ct_alpha2);
 }
 
 static double3 inv_dx_of(const teno_params *p)
@@ -339,6 +370,8 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.bc_lo = p->bc_lo[d];
         a.bc_hi = p->bc_hi[d];
         a.lam = &st->lam[d];
+        a.fast = g_fast_filter;
+        a.FK = fastk_of(p);
         a.K = K;
         const int slot = (g_prof.on && g_prof.used < ProfileRecord::kMax) ? g_prof.used++ : -1;
         if (slot >= 0) {
@@ -549,6 +582,29 @@ int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int n
     CUDA_TRY(cudaMemcpyAsync(&t, &st->t_accum, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (t_host) *t_host = t;
+    return TENO_OK;
+}
+
+int teno_reconstruct(const teno_params *p, const double *v, int64_t count, double *out,
+                     uint8_t *flags, void *stream)
+{
+    if (!p || (p->scheme != 8 && p->scheme != 10) || count < 0 || !v || !out) return TENO_EINVAL;
+    if (!(p->ct_cr > 0.0) || !(p->eps_beta >= 0.0) || !(p->eps_eta > 0.0)) return TENO_EINVAL;
+    if (count == 0) return TENO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Consts K = consts_of(p);
+    const FastK FK = fastk_of(p);
+    const int blk = 128, grd = grid_for(count, blk);
+    if (p->scheme == 8) recon_kernel<4><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
+    else recon_kernel<5><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
+    CUDA_TRY(cudaGetLastError());
+    return TENO_OK;
+}
+
+int teno_set_decision_filter(int on)
+{
+    if (on != 0 && on != 1) return TENO_EINVAL;
+    g_fast_filter = on;
     return TENO_OK;
 }
 

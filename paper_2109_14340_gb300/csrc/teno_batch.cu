@@ -98,7 +98,7 @@ __global__ void batch_finalize_kernel(const BatchProb *probs, int nprob, BatchSl
 template <int TF>
 __global__ void __launch_bounds__(TF) batch_face_kernel(
     const BatchProb *probs, int nprob, const int32_t *fprefix, const double *U, double *F,
-    BatchSlot *slots, Status *st, Consts K, int *counter)
+    BatchSlot *slots, Status *st, Consts K, FastK FK, int fast, int *counter)
 {
     extern __shared__ double sm[];
     __shared__ int s_item;
@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(TF) batch_face_kernel(
         a.bc_lo = d.bc_lo;
         a.bc_hi = d.bc_hi;
         a.lam = &slots[p].lam;
+        a.fast = fast;
+        a.FK = FK;
         a.K = K;
         a.K.limiter = d.limiter;
         const int64_t f0 = (int64_t)(it - fprefix[p]) * TF;
@@ -295,17 +297,19 @@ int enqueue_step(teno_batch *b, double *U, double cfl, char *ws, int tile_idx, i
     CUDA_TRY(cudaGetLastError());
     const int TF = kTiles[tile_idx];
     const int grid_f = b->num_sms * bps;
+    const FastK FK = fastk_make(b->common.ct_cr, b->common.ct_alpha1, b->common.ct_alpha2);
+    const int fast = g_fast_filter;
     for (int stg = 0; stg < 3; stg++) {
         const double *Uin = stg == 0 ? U : Us;
         if (TF == 64) {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 64>(), face_smem_bytes<1, 4, 1, 64>());
-            batch_face_kernel<64><<<grid_f, 64, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, counters + stg);
+            batch_face_kernel<64><<<grid_f, 64, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
         } else if (TF == 128) {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 128>(), face_smem_bytes<1, 4, 1, 128>());
-            batch_face_kernel<128><<<grid_f, 128, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, counters + stg);
+            batch_face_kernel<128><<<grid_f, 128, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
         } else {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 256>(), face_smem_bytes<1, 4, 1, 256>());
-            batch_face_kernel<256><<<grid_f, 256, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, counters + stg);
+            batch_face_kernel<256><<<grid_f, 256, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
         }
         CUDA_TRY(cudaGetLastError());
         batch_combine_kernel<<<grid_c, kCellTile, 0, s>>>(desc, np, cpre, Uin, U, stg == 2 ? U : Us, F,

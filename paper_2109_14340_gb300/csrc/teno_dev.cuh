@@ -67,17 +67,17 @@ __device__ __forceinline__ double scale_sep(double beta, double eps)
 }
 
 // Smoothness indicator of the large stencil S_L (Eq. TENO10_AA quadratic
-// forms) on data shifted by the cell-i value; terms of the zero shifted value
-// are skipped (they add exact zeros).
+// forms) on data shifted by the cell-i value, sh[m + H - 1] = v_m - v_0 for
+// the whole 2H stencil; terms of the zero shifted value are skipped (they add
+// exact zeros).
 template <int H, int L>
-__device__ __forceinline__ double beta_large(const double (&v)[2 * H])
+__device__ __forceinline__ double beta_large_s(const double (&sh)[2 * H])
 {
     constexpr int lo = (L == 3) ? -2 : (L == 4 ? -3 : -4);
     constexpr int w = 2 * L;
-    const double v0 = v[H - 1];
     double s[w];
 #pragma unroll
-    for (int r = 0; r < w; r++) s[r] = v[lo + r + H - 1] - v0;
+    for (int r = 0; r < w; r++) s[r] = sh[lo + r + H - 1];
     double acc = 0.0;
 #pragma unroll
     for (int r = 0; r < w; r++) {
@@ -93,6 +93,15 @@ __device__ __forceinline__ double beta_large(const double (&v)[2 * H])
         acc = (r == 0) ? s[r] * inner : fma(s[r], inner, acc);
     }
     return acc;
+}
+
+template <int H, int L>
+__device__ __forceinline__ double beta_large(const double (&v)[2 * H])
+{
+    double sh[2 * H];
+#pragma unroll
+    for (int r = 0; r < 2 * H; r++) sh[r] = v[r] - v[H - 1];
+    return beta_large_s<H, L>(sh);
 }
 
 template <int H, int L>

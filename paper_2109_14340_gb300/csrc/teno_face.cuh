@@ -10,6 +10,7 @@
 #pragma once
 
 #include "teno_dev.cuh"
+#include "teno_fast.cuh"
 
 namespace teno {
 
@@ -26,6 +27,8 @@ struct FaceArgs {
     int64_t ncell, nfaces;
     int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
     const double *lam;     // limiter's effective dt/dx for this direction (device)
+    int fast;              // 1: certified FP32 decision filter first
+    FastK FK;
     Consts K;
 };
 
@@ -59,7 +62,9 @@ struct SmemLayout {
 template <int ND, int H, int TP, int TF>
 constexpr size_t face_smem_bytes()
 {
-    return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP;
+    // staged cells + exact-path queue (values, results, decision bytes)
+    return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP +
+           sizeof(double) * (size_t)(2 * TP * TF) * (2 * H + 1) + (size_t)(2 * TP * TF);
 }
 
 // One tile: faces f0 .. f0+TF-1 along D of the TP pencils starting at x0
@@ -76,6 +81,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
 
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
+    __shared__ int qcount[nc];                 // exact-path queue length per field
+    if (threadIdx.x < nc) qcount[threadIdx.x] = 0;
 
     // Stage cells f0-H .. f0+TF+H-2 along D.
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
@@ -111,49 +118,74 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 
     const int p = threadIdx.x % TP, fo = threadIdx.x / TP;
     const int64_t f = f0 + fo;
-    if (f > nD || (D != 0 && x0 + p >= n0)) return;
+    const bool active = !(f > nD || (D != 0 && x0 + p >= n0));
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
-    (void)last;
 
-    // Roe average and eigenvectors (Sec. 5).
-    double ul[ND], ur[ND];
-#pragma unroll
-    for (int k = 0; k < ND; k++) { ul[k] = SQ(SL::QV + k, jl, p); ur[k] = SQ(SL::QV + k, jr, p); }
+    // Queue of reconstructions the certified filter leaves to the exact path,
+    // one counter per field; after the staged cells in shared memory.
+    constexpr int CAP = 2 * TP * TF;
+    double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
+    double *Qres = Qv + (size_t)CAP * W;              // [CAP]
+    uint8_t *Qfl = (uint8_t *)(Qres + CAP);           // [CAP]
+
     double Lm[nc][nc], Rm[nc][nc];
-    const double c2 = roe_eigensystem<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
-                                             SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
-    if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
-
-    int64_t flin;
-    if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
-    else if (D == 1) flin = x0 + p + n0 * (f + (n1 + 1) * z);
-    else flin = x0 + p + n0 * (y + n1 * f);
-
-    // Splitting speeds over the stencil (first maximum), or at recorded cells.
     double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
-    if (a.frozen_argmax) {
-        const unsigned w = a.frozen_argmax[flin];
-        am = SQ(SL::QLM, fo + (int)(w & 15), p);
-        a0 = SQ(SL::QL0, fo + (int)((w >> 4) & 15), p);
-        ap = SQ(SL::QLP, fo + (int)((w >> 8) & 15), p);
-        ar = SQ(SL::QLR, fo + (int)((w >> 12) & 15), p);
-    } else {
-        int jm = 0, j0 = 0, jp = 0, jr_ = 0;
+    int64_t flin = 0;
+    if (active) {
+        // Roe average and eigenvectors (Sec. 5).
+        double ul[ND], ur[ND];
 #pragma unroll
-        for (int j = 0; j < W; j++) {
-            const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
-            const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
-            if (j == 0 || em > am) { am = em; jm = j; }
-            if (j == 0 || e0 > a0) { a0 = e0; j0 = j; }
-            if (j == 0 || ep > ap) { ap = ep; jp = j; }
-            if (j == 0 || er > ar) { ar = er; jr_ = j; }
+        for (int k = 0; k < ND; k++) { ul[k] = SQ(SL::QV + k, jl, p); ur[k] = SQ(SL::QV + k, jr, p); }
+        const double c2 = roe_eigensystem<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
+                                                 SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
+        if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
+        if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
+        else if (D == 1) flin = x0 + p + n0 * (f + (n1 + 1) * z);
+        else flin = x0 + p + n0 * (y + n1 * f);
+        // Splitting speeds over the stencil (first maximum), or at recorded cells.
+        if (a.frozen_argmax) {
+            const unsigned w = a.frozen_argmax[flin];
+            am = SQ(SL::QLM, fo + (int)(w & 15), p);
+            a0 = SQ(SL::QL0, fo + (int)((w >> 4) & 15), p);
+            ap = SQ(SL::QLP, fo + (int)((w >> 8) & 15), p);
+            ar = SQ(SL::QLR, fo + (int)((w >> 12) & 15), p);
+        } else {
+            int jm = 0, j0 = 0, jp = 0, jr_ = 0;
+#pragma unroll
+            for (int j = 0; j < W; j++) {
+                const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
+                const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
+                if (j == 0 || em > am) { am = em; jm = j; }
+                if (j == 0 || e0 > a0) { a0 = e0; j0 = j; }
+                if (j == 0 || ep > ap) { ap = ep; jp = j; }
+                if (j == 0 || er > ar) { ar = er; jr_ = j; }
+            }
+            if (a.argmax) a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
         }
-        if (a.argmax) a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
     }
 
     double Fo[nc];
+#pragma unroll
+    for (int c = 0; c < nc; c++) Fo[c] = 0.0;
 #pragma unroll 1
     for (int k = 0; k < nc; k++) {
+        // Field k is a shear wave for 2 <= k < last: its left eigenvector row
+        // is (-u_t, e_t) and right column (0, e_t, u_t); the zero and unit
+        // entries are skipped (they add nothing / exactly the value).
+        const bool shear = (k >= 2 && k < last);
+        int tax = 0;
+        {
+            int kk = 2;
+#pragma unroll
+            for (int aa = 0; aa < ND; aa++) {
+                if (aa == D) continue;
+                if (kk == k) tax = aa;
+                kk++;
+            }
+        }
+        double val[2] = {0.0, 0.0};
+        uint8_t fls[2] = {0, 0};
+        int slot[2] = {-1, -1};
         double lrow[nc], rcol[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) {
@@ -164,46 +196,101 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             lrow[c] = lv;
             rcol[c] = rv;
         }
-        const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
-        double w[W], g[W];
+        if (active) {
+            const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
+            const double ha = 0.5 * alpha;
+            double w[W], hg[W];
 #pragma unroll
-        for (int j = 0; j < W; j++) {
-            double wv = lrow[0] * SQ(SL::QU, fo + j, p);
-            double gv = lrow[0] * SQ(SL::QF, fo + j, p);
+            for (int j = 0; j < W; j++) {
+                double wv, gv;
+                if (shear) {
+                    wv = SQ(SL::QU + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QU, fo + j, p);
+                    gv = SQ(SL::QF + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QF, fo + j, p);
+                } else {
+                    wv = lrow[0] * SQ(SL::QU, fo + j, p);
+                    gv = lrow[0] * SQ(SL::QF, fo + j, p);
 #pragma unroll
-            for (int c = 1; c < nc; c++) {
-                wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
-                gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
+                    for (int c = 1; c < nc; c++) {
+                        wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
+                        gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
+                    }
+                }
+                w[j] = wv;
+                hg[j] = 0.5 * gv;
             }
-            w[j] = wv;
-            g[j] = gv;
-        }
-        double hsum = 0.0;
 #pragma unroll 1
-        for (int s = 0; s < 2; s++) {
-            // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
-            const double sa = s ? -alpha : alpha;
-            double v[W];
+            for (int s = 0; s < 2; s++) {
+                // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
+                // v = (g +- alpha w)/2, as fma(+-alpha/2, w, g/2) (exact halving).
+                const double sa = s ? -ha : ha;
+                double v[W];
 #pragma unroll
-            for (int kk = 0; kk < W; kk++) {
-                const double wk = s ? w[W - 1 - kk] : w[kk];
-                const double gk = s ? g[W - 1 - kk] : g[kk];
-                v[kk] = 0.5 * fma(sa, wk, gk);
+                for (int kk = 0; kk < W; kk++) {
+                    const double wk = s ? w[W - 1 - kk] : w[kk];
+                    const double gk = s ? hg[W - 1 - kk] : hg[kk];
+                    v[kk] = fma(sa, wk, gk);
+                }
+                if (a.frozen) {
+                    fls[s] = a.frozen[(flin * nc + k) * 2 + s];
+                    val[s] = frozen_recon<H>(v, fls[s]);
+                    continue;
+                }
+                double sh[W];
+#pragma unroll
+                for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
+                const double bp = beta_large_s<H, H>(sh);
+                uint8_t fl = 0;
+                if (a.fast && fast_accept<H>(v, sh, bp, a.FK, fl)) {
+                    fls[s] = fl;
+                    val[s] = flux_large<H, H>(v);
+                } else {
+                    const int q = atomicAdd(&qcount[k], 1);
+                    slot[s] = q;
+#pragma unroll
+                    for (int kk = 0; kk < W; kk++) Qv[(size_t)q * W + kk] = v[kk];
+                }
             }
-            uint8_t fl;
-            double val;
-            if (a.frozen) {
-                fl = a.frozen[(flin * nc + k) * 2 + s];
-                val = frozen_recon<H>(v, fl);
-            } else {
-                val = teno_recon<H>(v, a.K, fl);
-            }
-            if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
-            hsum = s ? hsum + val : val;
         }
+        if (!a.frozen) {
+            // Drain the queue with every thread of the block: the exact path.
+            __syncthreads();
+            const int nq = qcount[k];
+            for (int q = threadIdx.x; q < nq; q += TP * TF) {
+                double v[W];
 #pragma unroll
-        for (int c = 0; c < nc; c++) Fo[c] = (k == 0) ? rcol[c] * hsum : fma(rcol[c], hsum, Fo[c]);
+                for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
+                uint8_t fl;
+                Qres[q] = teno_recon<H>(v, a.K, fl);
+                Qfl[q] = fl;
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+                    if (slot[s] >= 0) { val[s] = Qres[slot[s]]; fls[s] = Qfl[slot[s]]; }
+            }
+        }
+        if (active) {
+            if (a.flags) {
+                a.flags[(flin * nc + k) * 2] = fls[0];
+                a.flags[(flin * nc + k) * 2 + 1] = fls[1];
+            }
+            const double hsum = val[0] + val[1];
+            if (k == 0) {
+#pragma unroll
+                for (int c = 0; c < nc; c++) Fo[c] = rcol[c] * hsum;
+            } else if (shear) {
+#pragma unroll
+                for (int aa = 0; aa < ND; aa++)
+                    if (aa == tax) Fo[1 + aa] = Fo[1 + aa] + hsum;
+                Fo[last] = fma(rcol[last], hsum, Fo[last]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < nc; c++) Fo[c] = fma(rcol[c], hsum, Fo[c]);
+            }
+        }
     }
+    if (!active) return;
 
     if (a.K.limiter) {
         // Positivity-preserving flux limiter (cited in Sec. 5.3): blend toward

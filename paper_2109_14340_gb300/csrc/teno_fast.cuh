@@ -1,0 +1,282 @@
+// Certified single-precision decision filter for the TENO-AA reconstruction.
+//
+// The reconstruction's result depends on the smoothness indicators only
+// through discrete decisions: the C_T exponent [beta] of Eq. CT_definition and
+// the cut-off test chi_p >= C_T of the largest stencil (Eq. normalize, Eq.
+// cutoff).  This filter decides the common case -- "S_p is accepted, with
+// exponent n" -- in FP32 with rigorous error bounds, and says "uncertain"
+// whenever the bounds do not exclude the other outcome.  Only a certified
+// answer is used; the exact FP64 path (teno_recon) decides everything else, so
+// every decision equals the FP64 evaluation of the same formulas.
+//
+// FP64 parts kept: the shifted values s_m = v_m - v_0 and the largest
+// indicator beta_p (its printed quadratic form cancels about six orders of
+// magnitude on smooth data); they are computed with exactly the operations
+// of the exact path.  FP32 parts: the three small indicators, the scale
+// separation and normalisation (all the divisions), and the first-order
+// undivided-difference measure eta -> m -> g -> [beta].
+//
+// Error model: every FP32 operation is bounded by its relative rounding
+// 2^-24; conversions from FP64 truncate (relative error < 2^-23); the FP64
+// evaluation of the same formulas differs from the exact value by a few 2^-53,
+// covered by the widening factors.  Operands are scaled by a power of two
+// (exact) so that FP32 never over- or underflows; epsilon = 1e-40 of Eq.
+// scale_separation and of the eta measure is handled by requiring the
+// indicators (in original units) to exceed 2^-100, where it is negligible.
+#pragma once
+
+#include <cmath>
+
+#include "teno_dev.cuh"
+
+namespace teno {
+
+// Per-launch constants of the filter.
+struct FastK {
+    float cr_inv_lo, cr_inv_hi;  // 1 / C_r rounded down / up
+    float alpha1, alpha2;
+    int nexp_smooth;             // [beta] at m = 0, as the exact path computes it
+    float thr[23];               // thr[n] <= 1 / (10^-n (1 + 2^-16)) - 1
+};
+
+// Filter switch (teno_set_decision_filter), process-wide.
+extern int g_fast_filter;
+
+// Host: constants of the filter for given C_T parameters.
+inline FastK fastk_make(double cr, double alpha1, double alpha2)
+{
+    FastK F;
+    const double inv = 1.0 / cr;
+    F.cr_inv_lo = nextafterf((float)inv, 0.0f);
+    F.cr_inv_hi = nextafterf((float)inv, 1e30f);
+    F.alpha1 = (float)alpha1;
+    F.alpha2 = (float)alpha2;
+    const double bct = alpha1 - alpha2 * (1.0 - 1.0);
+    const double fl = floor(bct);
+    F.nexp_smooth = fl < 0.0 ? 0 : (fl > 22.0 ? 22 : (int)fl);
+    for (int n = 0; n < 23; n++) {
+        const double t = 1.0 / (pow(10.0, -n) * (1.0 + 1.0 / 65536.0)) - 1.0;
+        // round down (toward -inf), then one more step: a safe lower bound
+        float tf = (float)t;
+        if ((double)tf > t) tf = nextafterf(tf, -INFINITY);
+        F.thr[n] = nextafterf(tf, -INFINITY);
+    }
+    return F;
+}
+
+// FP64 -> FP32 with the exponent lowered by `shift` (exact power-of-two
+// scaling), truncating the mantissa.  Scaled magnitudes below 2^-100 become
+// zero (absolute error < 2^-100, which callers add to their bounds); ok =
+// false above 2^100 or for subnormal inputs.
+__device__ __forceinline__ float d2f_scaled(double x, int shift, bool &ok)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int e = (hi >> 20) & 0x7FF;
+    if (e == 0) {
+        if ((hi & 0xFFFFF) == 0 && lo == 0) return 0.0f;   // +-0
+        ok = false;
+        return 0.0f;
+    }
+    const int ef = e - 1023 - shift;                         // unbiased scaled exponent
+    if (ef < -100) return 0.0f;
+    if (ef > 100) {
+        ok = false;
+        return 0.0f;
+    }
+    const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(ef + 127) << 23) |
+                          (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ int dexp(double x)
+{
+    return ((__double2hiint(x) >> 20) & 0x7FF) - 1023;
+}
+
+__device__ __forceinline__ bool dbits_equal(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// Bounds [lo, hi] of eta = (|2ab| + eps)/(a^2 + b^2 + eps) from FP32 values
+// a, b with absolute error bounds ea, eb (scaled units), and the exact-zero
+// knowledge of the FP64 differences.  tiny: scaled 2^-100 threshold.
+__device__ __forceinline__ void eta_bounds(float a, float ea, bool za, float b, float eb, bool zb,
+                                           float tiny2, float &lo, float &hi)
+{
+    if (za && zb) { lo = 1.0f; hi = 1.0f; return; }          // (0 + eps) / (0 + eps)
+    if (za || zb) {                                           // eps / (d^2 + eps)
+        const float d = za ? fabsf(b) - eb : fabsf(a) - ea;
+        lo = 0.0f;
+        hi = (d > 0.0f && d * d >= tiny2) ? 1e-9f : 1.0f;
+        return;
+    }
+    const float al = fabsf(a) - ea, ah = fabsf(a) + ea;
+    const float bl = fabsf(b) - eb, bh = fabsf(b) + eb;
+    if (!(al > 1e-30f) || !(bl > 1e-30f)) { lo = 0.0f; hi = 1.0f; return; }
+    const float t1 = __fdividef(bl, ah), t2 = __fdividef(bh, al);   // t1 <= t2
+    const float e1 = __fdividef(2.0f * t1, 1.0f + t1 * t1);
+    const float e2 = __fdividef(2.0f * t2, 1.0f + t2 * t2);
+    lo = fminf(e1, e2) * (1.0f - 1.0e-5f);
+    float h = (t1 <= 1.0f && t2 >= 1.0f) ? 1.0f : fmaxf(e1, e2) * (1.0f + 1.0e-5f);
+    if (!(al * al + bl * bl >= tiny2)) h = 1.0f;             // eps may matter
+    hi = fminf(h + 1e-9f, 1.0f);
+}
+
+// g(m) = ((1-m)^2)^2 (1+4m) in FP32.
+__device__ __forceinline__ float g_of_m(float m)
+{
+    const float om = 1.0f - m;
+    const float om2 = om * om;
+    return (om2 * om2) * (1.0f + 4.0f * m);
+}
+
+// Bounds of a small indicator 1/4 a^2 + 13/12 b^2 given FP32 a, b and their
+// absolute error bounds.
+__device__ __forceinline__ void small_beta(float a, float ea, float b, float eb, float &beta,
+                                           float &err)
+{
+    const float c13 = 13.0f / 12.0f;
+    beta = 0.25f * (a * a) + c13 * (b * b);
+    const float aa = fabsf(a), ab = fabsf(b);
+    err = 0.25f * (2.0f * aa * ea + ea * ea) + 1.0834f * (2.0f * ab * eb + eb * eb) +
+          beta * 1.0e-6f;
+}
+
+// The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
+// (s[H-1] == 0); beta_p: the largest stencil's indicator as the exact path
+// computes it.  Returns true with the decision byte when "S_p accepted with
+// exponent n" is certain.
+template <int H>
+__device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const double (&s)[2 * H],
+                                            double beta_p, const FastK &F, uint8_t &flag)
+{
+    constexpr int W = 2 * H;
+#define SV(m) s[(m) + H - 1]
+#define VV(m) v[(m) + H - 1]
+    // All values bit-identical: every indicator is exactly 0, chi = 1/4,
+    // eta = 1, hence S_p with the smooth exponent.
+    bool all_eq = true;
+#pragma unroll
+    for (int j = 0; j < W; j++) all_eq = all_eq && dbits_equal(v[j], v[H - 1]);
+    if (all_eq) {
+        flag = (uint8_t)((H - 2) | (((F.nexp_smooth - 7) & 7) << 5));
+        return true;
+    }
+    // Common scale: the largest exponent among the shifted values.
+    int emax = -1100;
+#pragma unroll
+    for (int j = 0; j < W; j++)
+        if (j != H - 1 && (__double2hiint(s[j]) & 0x7FF00000) != 0) emax = max(emax, dexp(s[j]));
+    if (emax < -900 || emax > 900) return false;
+    bool ok = true;
+    float f[W];
+#pragma unroll
+    for (int j = 0; j < W; j++) f[j] = (j == H - 1) ? 0.0f : d2f_scaled(s[j], emax, ok);
+    if (!ok) return false;
+    // indicator threshold 2^-100 in original units -> scaled units
+    const int tb = -100 - 2 * emax;
+    if (tb > 100) return false;
+    const float tiny2 = tb < -126 ? 1.17549435e-38f : __uint_as_float((unsigned)(tb + 127) << 23);
+    const float u23 = 1.1920929e-7f * 1.0001f, u24 = 5.9604645e-8f * 1.0001f;
+    const float z100 = 1.6e-30f;             // > 2^-100: flushed-value error
+    // The exact path evaluates the small indicators on the unshifted values:
+    // its rounding is relative to max |v| (bound 2^(ev - emax - 50) scaled).
+    int ev = -1100;
+#pragma unroll
+    for (int j = 0; j < W; j++)
+        if ((__double2hiint(v[j]) & 0x7FF00000) != 0) ev = max(ev, dexp(v[j]));
+    if (ev - emax > 60) return false;
+    const float eo = ev < -900 ? 0.0f : __uint_as_float((unsigned)(max(ev - emax - 50, -126) + 127) << 23);
+#define FF(m) f[(m) + H - 1]
+
+    // eta measure over cells -1..2 from the differences Delta_{m+1/2}, m=-2..2.
+    float dl[5], el[5];
+    bool zl[5];
+#pragma unroll
+    for (int m = -2; m <= 2; m++) {
+        const float a = FF(m + 1), b = FF(m);
+        dl[m + 2] = a - b;
+        el[m + 2] = u23 * (fabsf(a) + fabsf(b)) + u24 * fabsf(dl[m + 2]) + 2.0f * z100;
+        zl[m + 2] = dbits_equal(VV(m + 1), VV(m));
+    }
+    float emin_lo = 1.0f, emin_hi = 1.0f;
+#pragma unroll
+    for (int j = -1; j <= 2; j++) {
+        float lo, hi;
+        eta_bounds(dl[j + 2], el[j + 2], zl[j + 2], dl[j + 1], el[j + 1], zl[j + 1], tiny2, lo, hi);
+        emin_lo = fminf(emin_lo, lo);
+        emin_hi = fminf(emin_hi, hi);
+    }
+    int nexp;
+    const float r_lo = emin_lo * F.cr_inv_lo * (1.0f - 2.5e-7f);
+    if (r_lo >= 1.0f) {
+        nexp = F.nexp_smooth;                  // eta >= C_r: m = 0 exactly
+    } else {
+        const float r_hi = emin_hi * F.cr_inv_hi * (1.0f + 2.5e-7f);
+        const float m_lo = fmaxf(1.0f - fminf(1.0f, r_hi) - 2.5e-7f, 0.0f);
+        const float m_hi = fminf(1.0f - fminf(1.0f, r_lo) + 2.5e-7f, 1.0f);
+        const float g_lo = g_of_m(m_hi) * (1.0f - 1.0e-6f);
+        const float g_hi = g_of_m(m_lo) * (1.0f + 1.0e-6f);
+        const float b_lo = F.alpha1 - F.alpha2 * (1.0f - g_lo) - 1.0e-4f;
+        const float b_hi = F.alpha1 - F.alpha2 * (1.0f - g_hi) + 1.0e-4f;
+        int n_lo = (int)floorf(b_lo), n_hi = (int)floorf(b_hi);
+        n_lo = n_lo < 0 ? 0 : (n_lo > 22 ? 22 : n_lo);
+        n_hi = n_hi < 0 ? 0 : (n_hi > 22 ? 22 : n_hi);
+        if (!(b_lo == b_lo) || !(b_hi == b_hi) || n_lo != n_hi) return false;
+        nexp = n_lo;
+    }
+
+    // Small indicators on the shifted values (s_0 = 0).
+    float b0, e0, b1, e1, b2, e2;
+    {
+        const float slack = 2.0f * z100 + 4.0f * eo;
+        const float a = FF(-1) - FF(1);
+        const float ea = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(a) + slack;
+        const float b = FF(-1) + FF(1);
+        const float eb = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b0, e0);
+    }
+    {
+        const float slack = 5.0f * z100 + 8.0f * eo;
+        const float a = FF(2) - 4.0f * FF(1);
+        const float ea = u23 * (fabsf(FF(2)) + 4.0f * fabsf(FF(1))) + u24 * fabsf(a) + slack;
+        const float b = FF(2) - 2.0f * FF(1);
+        const float eb = u23 * (fabsf(FF(2)) + 2.0f * fabsf(FF(1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b1, e1);
+    }
+    {
+        const float slack = 5.0f * z100 + 8.0f * eo;
+        const float a = FF(-2) - 4.0f * FF(-1);
+        const float ea = u23 * (fabsf(FF(-2)) + 4.0f * fabsf(FF(-1))) + u24 * fabsf(a) + slack;
+        const float b = FF(-2) - 2.0f * FF(-1);
+        const float eb = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b2, e2);
+    }
+    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;      // lower bounds (eps dropped)
+    if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
+    // beta_p (FP64, exact-path value) -> scaled FP32 upper bound
+    if (!(beta_p > 0.0)) return false;
+    bool okp = true;
+    const float bp = d2f_scaled(beta_p, 2 * emax, okp);
+    if (!okp || !(bp >= tiny2)) return false;
+    const float xp = bp * (1.0f + 2.5e-7f);
+    // chi_p >= C_T  <=>  sum_k (x_p / x_k)^7 <= 1/C_T - 1
+    float tsum = 0.0f;
+    {
+        const float r0 = __fdividef(xp, x0) * (1.0f + 5e-7f);
+        const float r1 = __fdividef(xp, x1) * (1.0f + 5e-7f);
+        const float r2 = __fdividef(xp, x2) * (1.0f + 5e-7f);
+        const float q0 = r0 * r0, q1 = r1 * r1, q2 = r2 * r2;
+        tsum = (q0 * q0 * q0 * r0 + q1 * q1 * q1 * r1 + q2 * q2 * q2 * r2) * (1.0f + 2e-6f);
+    }
+    if (!(tsum <= F.thr[nexp])) return false;
+    flag = (uint8_t)((H - 2) | (((nexp - 7) & 7) << 5));
+    return true;
+#undef FF
+#undef SV
+#undef VV
+}
+
+}  // namespace teno

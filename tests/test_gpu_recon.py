@@ -1,0 +1,159 @@
+"""The GPU's scalar TENO-AA reconstruction (teno_reconstruct) against the
+oracle, stencil by stencil, with the certified single-precision decision
+filter on and off.  Besides random smooth / rough / near-constant /
+degenerate data, the stencils include adversarial families placed on the
+decision thresholds by bisection with the oracle: chi_p = C_T (Eq. cutoff),
+eta = C_r (Eq. m_definition) and every integer boundary of [beta] in Eq.
+CT_definition, each probed at the neighbouring doubles.  Values must agree
+bitwise and the decision bytes exactly."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2109_14340_gb300 as T  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def oracle_batch(scheme, V):
+    p = oracle.params(1, [16], [1.0], scheme=scheme)
+    out = np.empty(len(V))
+    fl = np.empty(len(V), np.uint8)
+    for i, v in enumerate(V):
+        out[i], fl[i] = oracle.recon(p, v)
+    return out, fl
+
+
+def gpu_batch(scheme, V, fast):
+    p = T.teno_params_init(scheme=scheme)
+    T.teno_set_decision_filter(fast)
+    try:
+        v = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
+        out = torch.empty(len(V), dtype=torch.float64, device=DEV)
+        fl = torch.empty(len(V), dtype=torch.uint8, device=DEV)
+        T.teno_reconstruct(p, v, out, fl)
+        return out.cpu().numpy(), fl.cpu().numpy()
+    finally:
+        T.teno_set_decision_filter(True)
+
+
+def neighbours(x, k=3):
+    out = [x]
+    lo = hi = x
+    for _ in range(k):
+        lo = np.nextafter(lo, -np.inf)
+        hi = np.nextafter(hi, np.inf)
+        out += [lo, hi]
+    return out
+
+
+def bisect(make, a, b, key, iters=200):
+    """Boundary of key(oracle(make(x))) between a and b (key differs there)."""
+    p = None
+    ka = key(make(a))
+    kb = key(make(b))
+    if ka == kb:
+        return None
+    for _ in range(iters):
+        m = 0.5 * (a + b)
+        if m == a or m == b:
+            break
+        if key(make(m)) == ka:
+            a = m
+        else:
+            b = m
+    return a, b
+
+
+def adversarial(scheme):
+    H = scheme // 2
+    offs = np.arange(-H + 1, H + 1, dtype=float)
+    po = oracle.params(1, [16], [1.0], scheme=scheme)
+    key_sel = lambda v: oracle.recon(po, v)[1] & 3
+    key_ct = lambda v: (oracle.recon(po, v)[1] >> 5) & 7
+    out = []
+    # chi_p = C_T: a step at the largest stencil's edge, C_T = 1e-14 region
+    for base_scale in (1.0, 1e-3, 1e4):
+        def make(lam, bs=base_scale):
+            return bs * (np.sin(0.3 * offs) + 2.0 + lam * (offs >= H))
+        r = bisect(make, 0.0, 10.0, key_sel)
+        if r:
+            for x in neighbours(r[0]) + neighbours(r[1]):
+                out.append(make(x))
+    # eta = C_r and every [beta] boundary: slope change at the upwind cell
+    def make_t(t):
+        d = np.where(offs < 0, 1.0, t)
+        return np.concatenate([[0.0], np.cumsum(d[1:])]) + 5.0
+    ts = np.linspace(1e-4, 1.0, 400)
+    cts = [key_ct(make_t(t)) for t in ts]
+    for i in range(1, len(ts)):
+        if cts[i] != cts[i - 1]:
+            r = bisect(make_t, ts[i - 1], ts[i], key_ct)
+            if r:
+                for x in neighbours(r[0]) + neighbours(r[1]):
+                    out.append(make_t(x))
+    # chi_p = C_T with C_T in the adaptive (non-smooth) range
+    for t0 in (0.05, 0.1, 0.2):
+        def make2(lam, t0=t0):
+            return make_t(t0) + lam * (offs >= H)
+        r = bisect(make2, 0.0, 50.0, key_sel)
+        if r:
+            for x in neighbours(r[0]) + neighbours(r[1]):
+                out.append(make2(x))
+    return np.array(out)
+
+
+def random_stencils(scheme, n=20000, seed=7):
+    g = np.random.Generator(np.random.PCG64(seed))
+    W = scheme
+    offs = np.arange(W, dtype=float)
+    V = []
+    for i in range(n):
+        kind = i % 6
+        scale = 10.0 ** g.uniform(-8, 8)
+        shift = g.uniform(-1, 1) * 10.0 ** g.uniform(-2, 6)
+        if kind == 0:      # smooth
+            v = np.sin(g.uniform(0.01, 1.2) * offs + g.uniform(0, 6)) * scale + shift
+        elif kind == 1:    # rough
+            v = g.standard_normal(W) * scale + shift
+        elif kind == 2:    # step somewhere
+            v = (offs >= g.integers(0, W)).astype(float) * scale + shift + 1e-3 * scale * np.sin(offs)
+        elif kind == 3:    # near-constant: rounding-level variation
+            v = shift + 1.0 + np.abs(shift) * 1e-15 * g.standard_normal(W)
+        elif kind == 4:    # ghost-like: constant run then smooth
+            k = g.integers(1, W)
+            v = np.sin(0.2 * offs) * scale + shift
+            v[:k] = v[k]
+        else:              # polynomial (smooth, exact linear recovery)
+            v = (g.uniform(-1, 1) + g.uniform(-1, 1) * offs + g.uniform(-0.1, 0.1) * offs ** 2) * scale
+        V.append(v)
+    V.append(np.zeros(W))
+    V.append(np.full(W, 3.5))
+    return np.array(V)
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+def test_reconstruction_matches_oracle(scheme):
+    V = np.concatenate([random_stencils(scheme), adversarial(scheme)])
+    ref, rfl = oracle_batch(scheme, V)
+    for fast in (True, False):
+        out, fl = gpu_batch(scheme, V, fast)
+        bad = np.nonzero((fl != rfl) | (out.view(np.int64) != ref.view(np.int64)))[0]
+        assert bad.size == 0, (fast, bad[:10], fl[bad[:5]], rfl[bad[:5]])
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+def test_adversarial_families_reach_both_sides(scheme):
+    """The bisected families really straddle thresholds (both outcomes)."""
+    V = adversarial(scheme)
+    _, rfl = oracle_batch(scheme, V)
+    assert len(V) > 50
+    assert len(set((rfl & 3).tolist())) >= 2
+    assert len(set(((rfl >> 5) & 7).tolist())) >= 5

@@ -62,9 +62,11 @@ struct SmemLayout {
 template <int ND, int H, int TP, int TF>
 constexpr size_t face_smem_bytes()
 {
-    // staged cells + exact-path queue (values, results, decision bytes)
+    // staged cells + exact-path queue (values, owners) + per-thread results
     return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP +
-           sizeof(double) * (size_t)(2 * TP * TF) * (2 * H + 1) + (size_t)(2 * TP * TF);
+           sizeof(double) * (size_t)(2 * TP * TF) * (2 * H) +
+           sizeof(double) * (size_t)(TP * TF) * 2 * (ND + 2) + sizeof(int) * (size_t)(2 * TP * TF) +
+           (size_t)(TP * TF) * 2 * (ND + 2);
 }
 
 // One tile: faces f0 .. f0+TF-1 along D of the TP pencils starting at x0
@@ -81,8 +83,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
 
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
-    __shared__ int qcount[nc];                 // exact-path queue length per field
-    if (threadIdx.x < nc) qcount[threadIdx.x] = 0;
+    __shared__ int qcount[1];                  // exact-path queue length
+    if (threadIdx.x == 0) qcount[0] = 0;
 
     // Stage cells f0-H .. f0+TF+H-2 along D.
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
@@ -121,12 +123,13 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     const bool active = !(f > nD || (D != 0 && x0 + p >= n0));
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
 
-    // Queue of reconstructions the certified filter leaves to the exact path,
-    // one counter per field; after the staged cells in shared memory.
+    // Queue of reconstructions the certified filter leaves to the exact path
+    // (values, owner), and per-thread result slots; after the staged cells.
     constexpr int CAP = 2 * TP * TF;
     double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
-    double *Qres = Qv + (size_t)CAP * W;              // [CAP]
-    uint8_t *Qfl = (uint8_t *)(Qres + CAP);           // [CAP]
+    double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]
+    int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
+    uint8_t *Qfl = (uint8_t *)(Qmeta + CAP);          // [threads][2 nc]
 
     double Lm[nc][nc], Rm[nc][nc];
     double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
@@ -164,14 +167,16 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         }
     }
 
-    double Fo[nc];
+    // Split-flux reconstructions of every field and sign: certified ones now,
+    // the rest queued (or, if the queue is full, done in place) and drained
+    // once per tile by the whole block with the exact path.
+    double hv[2 * nc];                 // the two reconstructed values per field
 #pragma unroll
-    for (int c = 0; c < nc; c++) Fo[c] = 0.0;
+    for (int q = 0; q < 2 * nc; q++) hv[q] = 0.0;
+    unsigned pending = 0;              // bit 2k+s: value comes from the queue
 #pragma unroll 1
     for (int k = 0; k < nc; k++) {
-        // Field k is a shear wave for 2 <= k < last: its left eigenvector row
-        // is (-u_t, e_t) and right column (0, e_t, u_t); the zero and unit
-        // entries are skipped (they add nothing / exactly the value).
+        if (!active) break;
         const bool shear = (k >= 2 && k < last);
         int tax = 0;
         {
@@ -183,110 +188,130 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 kk++;
             }
         }
-        double val[2] = {0.0, 0.0};
-        uint8_t fls[2] = {0, 0};
-        int slot[2] = {-1, -1};
-        double lrow[nc], rcol[nc];
+        double lrow[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) {
-            double lv = Lm[0][c], rv = Rm[c][0];
+            double lv = Lm[0][c];
 #pragma unroll
             for (int kk = 1; kk < nc; kk++)
-                if (k == kk) { lv = Lm[kk][c]; rv = Rm[c][kk]; }
+                if (k == kk) lv = Lm[kk][c];
             lrow[c] = lv;
-            rcol[c] = rv;
         }
-        if (active) {
-            const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
-            const double ha = 0.5 * alpha;
-            double w[W], hg[W];
+        const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
+        const double ha = 0.5 * alpha;
+        double w[W], hg[W];
 #pragma unroll
-            for (int j = 0; j < W; j++) {
-                double wv, gv;
-                if (shear) {
-                    wv = SQ(SL::QU + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QU, fo + j, p);
-                    gv = SQ(SL::QF + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QF, fo + j, p);
-                } else {
-                    wv = lrow[0] * SQ(SL::QU, fo + j, p);
-                    gv = lrow[0] * SQ(SL::QF, fo + j, p);
+        for (int j = 0; j < W; j++) {
+            double wv, gv;
+            if (shear) {
+                wv = SQ(SL::QU + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QU, fo + j, p);
+                gv = SQ(SL::QF + 1 + tax, fo + j, p) + lrow[0] * SQ(SL::QF, fo + j, p);
+            } else {
+                wv = lrow[0] * SQ(SL::QU, fo + j, p);
+                gv = lrow[0] * SQ(SL::QF, fo + j, p);
 #pragma unroll
-                    for (int c = 1; c < nc; c++) {
-                        wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
-                        gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
-                    }
+                for (int c = 1; c < nc; c++) {
+                    wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
+                    gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
                 }
-                w[j] = wv;
-                hg[j] = 0.5 * gv;
             }
+            w[j] = wv;
+            hg[j] = 0.5 * gv;
+        }
 #pragma unroll 1
-            for (int s = 0; s < 2; s++) {
-                // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
-                // v = (g +- alpha w)/2, as fma(+-alpha/2, w, g/2) (exact halving).
-                const double sa = s ? -ha : ha;
-                double v[W];
+        for (int s = 0; s < 2; s++) {
+            // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
+            // v = (g +- alpha w)/2, as fma(+-alpha/2, w, g/2) (exact halving).
+            const double sa = s ? -ha : ha;
+            double v[W];
 #pragma unroll
-                for (int kk = 0; kk < W; kk++) {
-                    const double wk = s ? w[W - 1 - kk] : w[kk];
-                    const double gk = s ? hg[W - 1 - kk] : hg[kk];
-                    v[kk] = fma(sa, wk, gk);
-                }
-                if (a.frozen) {
-                    fls[s] = a.frozen[(flin * nc + k) * 2 + s];
-                    val[s] = frozen_recon<H>(v, fls[s]);
-                    continue;
-                }
+            for (int kk = 0; kk < W; kk++) {
+                const double wk = s ? w[W - 1 - kk] : w[kk];
+                const double gk = s ? hg[W - 1 - kk] : hg[kk];
+                v[kk] = fma(sa, wk, gk);
+            }
+            double val = 0.0;
+            uint8_t fl = 0;
+            bool done = true;
+            if (a.frozen) {
+                fl = a.frozen[(flin * nc + k) * 2 + s];
+                val = frozen_recon<H>(v, fl);
+            } else {
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
                 const double bp = beta_large_s<H, H>(sh);
-                uint8_t fl = 0;
                 if (a.fast && fast_accept<H>(v, sh, bp, a.FK, fl)) {
-                    fls[s] = fl;
-                    val[s] = flux_large<H, H>(v);
+                    val = flux_large<H, H>(v);
                 } else {
-                    const int q = atomicAdd(&qcount[k], 1);
-                    slot[s] = q;
+                    const int q = atomicAdd(&qcount[0], 1);
+                    if (q < CAP) {
 #pragma unroll
-                    for (int kk = 0; kk < W; kk++) Qv[(size_t)q * W + kk] = v[kk];
+                        for (int kk = 0; kk < W; kk++) Qv[(size_t)q * W + kk] = v[kk];
+                        Qmeta[q] = (threadIdx.x << 4) | (2 * k + s);
+                        pending |= 1u << (2 * k + s);
+                        done = false;
+                    } else {
+                        val = teno_recon<H>(v, a.K, fl);      // queue full: in place
+                    }
+                }
+            }
+            if (done) {
+#pragma unroll
+                for (int q = 0; q < 2 * nc; q++)
+                    if (q == 2 * k + s) hv[q] = val;
+                if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
+            }
+        }
+    }
+    if (!a.frozen) {
+        __syncthreads();
+        const int nq = min(qcount[0], CAP);
+        for (int q = threadIdx.x; q < nq; q += TP * TF) {
+            double v[W];
+#pragma unroll
+            for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
+            uint8_t fl;
+            const double r = teno_recon<H>(v, a.K, fl);
+            const int meta = Qmeta[q];
+            Qres[(meta >> 4) * (2 * nc) + (meta & 15)] = r;
+            Qfl[(meta >> 4) * (2 * nc) + (meta & 15)] = fl;
+        }
+        __syncthreads();
+        if (active && pending) {
+#pragma unroll
+            for (int q = 0; q < 2 * nc; q++) {
+                if (pending & (1u << q)) {
+                    hv[q] = Qres[threadIdx.x * (2 * nc) + q];
+                    if (a.flags) a.flags[(flin * nc + (q >> 1)) * 2 + (q & 1)] = Qfl[threadIdx.x * (2 * nc) + q];
                 }
             }
         }
-        if (!a.frozen) {
-            // Drain the queue with every thread of the block: the exact path.
-            __syncthreads();
-            const int nq = qcount[k];
-            for (int q = threadIdx.x; q < nq; q += TP * TF) {
-                double v[W];
+    }
+
+    // Back-projection F = sum_k r_k (f+_k + f-_k), fields ascending; the zero
+    // and unit entries of the shear columns are skipped.
+    double Fo[nc];
+    if (active) {
 #pragma unroll
-                for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
-                uint8_t fl;
-                Qres[q] = teno_recon<H>(v, a.K, fl);
-                Qfl[q] = fl;
-            }
-            __syncthreads();
-            if (active) {
-#pragma unroll
-                for (int s = 0; s < 2; s++)
-                    if (slot[s] >= 0) { val[s] = Qres[slot[s]]; fls[s] = Qfl[slot[s]]; }
-            }
-        }
-        if (active) {
-            if (a.flags) {
-                a.flags[(flin * nc + k) * 2] = fls[0];
-                a.flags[(flin * nc + k) * 2 + 1] = fls[1];
-            }
-            const double hsum = val[0] + val[1];
+        for (int k = 0; k < nc; k++) {
+            const double hsum = hv[2 * k] + hv[2 * k + 1];
             if (k == 0) {
 #pragma unroll
-                for (int c = 0; c < nc; c++) Fo[c] = rcol[c] * hsum;
-            } else if (shear) {
+                for (int c = 0; c < nc; c++) Fo[c] = Rm[c][0] * hsum;
+            } else if (k >= 2 && k < last) {
+                int tax = 0, kk = 2;
 #pragma unroll
-                for (int aa = 0; aa < ND; aa++)
-                    if (aa == tax) Fo[1 + aa] = Fo[1 + aa] + hsum;
-                Fo[last] = fma(rcol[last], hsum, Fo[last]);
+                for (int aa = 0; aa < ND; aa++) {
+                    if (aa == D) continue;
+                    if (kk == k) tax = aa;
+                    kk++;
+                }
+                Fo[1 + tax] = Fo[1 + tax] + hsum;
+                Fo[last] = fma(Rm[last][k], hsum, Fo[last]);
             } else {
 #pragma unroll
-                for (int c = 0; c < nc; c++) Fo[c] = fma(rcol[c], hsum, Fo[c]);
+                for (int c = 0; c < nc; c++) Fo[c] = fma(Rm[c][k], hsum, Fo[c]);
             }
         }
     }
@@ -365,7 +390,7 @@ __global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
 template <int ND, int H, int D>
 cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
 {
-    constexpr int TP = (D == 0) ? 1 : 32;
+    constexpr int TP = (D == 0) ? 1 : 16;
     constexpr int TF = (D == 0) ? 128 : 8;
     constexpr size_t smem = face_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;

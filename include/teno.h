@@ -295,11 +295,16 @@ int teno_set_decision_filter(int on);
  * brackets every face-sweep launch with a pair of CUDA events recorded on
  * the launch's stream (at most 8192 launches are recorded); (0) stops.
  * teno_profile_read synchronises the recorded events and returns the summed
- * device milliseconds, the number of launches and the number of faces they
- * computed.  Not safe to call concurrently from several host threads.  The
- * paper has no counterpart: this is measurement support. */
+ * device milliseconds, the number of launches, the number of faces they
+ * computed and how many of their reconstructions took the exact FP64 path
+ * (the rest were decided by the single-precision filter; each face has
+ * 2 (ndim + 2) reconstructions).  Any output pointer may be NULL.
+ * teno_profile_enable(1) allocates an 8-byte device counter once (kept
+ * until the context ends) and synchronises the device.  Not safe to call concurrently from
+ * several host threads.  The paper has no counterpart: this is measurement
+ * support. */
 int teno_profile_enable(int on);
-int teno_profile_read(double *ms, int64_t *launches, int64_t *faces);
+int teno_profile_read(double *ms, int64_t *launches, int64_t *faces, int64_t *exact_recons);
 
 /* Human-readable text of a return code (static storage). */
 const char *teno_strerror(int code);

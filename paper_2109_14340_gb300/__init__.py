@@ -105,6 +105,7 @@ def load():
         lib.teno_reconstruct.argtypes = [P, vp, ctypes.c_int64, vp, vp, vp]
         lib.teno_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]
         lib.teno_strerror.argtypes = [ctypes.c_int]
         lib.teno_strerror.restype = ctypes.c_char_p
@@ -257,13 +258,15 @@ def teno_profile_enable(on: bool = True):
 
 
 def teno_profile_read():
-    """(milliseconds, launches, faces) of the recorded face-sweep launches."""
+    """(milliseconds, launches, faces, exact-path reconstructions) of the
+    recorded face-sweep launches."""
     ms = ctypes.c_double()
     nl = ctypes.c_int64()
     nf = ctypes.c_int64()
-    _check(load().teno_profile_read(ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nf)),
-           "teno_profile_read")
-    return ms.value, nl.value, nf.value
+    ne = ctypes.c_int64()
+    _check(load().teno_profile_read(ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nf),
+                                    ctypes.byref(ne)), "teno_profile_read")
+    return ms.value, nl.value, nf.value, ne.value
 
 
 # ---------------------------------------------------------------------------

@@ -99,6 +99,83 @@ def sym_norms(M, lo, w):
     return n1 * 1.01, n2 * 1.01
 
 
+def ldl_factors(spec):
+    """Exact rational L D L^T of the indicator form on the shifted values
+    (offset 0 removed), variables in DESCENDING offset: beta = sum_i D_i y_i^2
+    with y_i = sum_{m >= i} L[m][i] s_{off(m)}.  Every D_i > 0 (the form is
+    positive definite).  The descending order gives the smaller single-
+    precision error bounds on smooth data."""
+    from fractions import Fraction as Fr
+    den, lo, terms = spec
+    w = -2 * lo + 2
+    idx = [r for r in range(w) if r + lo != 0][::-1]
+    M = {}
+    for a, b, c in terms:
+        M[(min(a, b) - lo, max(a, b) - lo)] = Fr(c, den)
+    n = len(idx)
+    A = [[Fr(0)] * n for _ in range(n)]
+    for i, r in enumerate(idx):
+        for j, t in enumerate(idx):
+            if r == t:
+                A[i][j] = M[(r, r)]
+            else:
+                A[i][j] = M[(min(r, t), max(r, t))] / 2
+    L = [[Fr(int(i == j)) for j in range(n)] for i in range(n)]
+    D = [Fr(0)] * n
+    for j in range(n):
+        D[j] = A[j][j] - sum(L[j][k] ** 2 * D[k] for k in range(j))
+        assert D[j] > 0
+        for i in range(j + 1, n):
+            L[i][j] = (A[i][j] - sum(L[i][k] * L[j][k] * D[k] for k in range(j))) / D[j]
+    return [r + lo for r in idx], L, D
+
+
+def f32_up(x):
+    """Smallest float32 >= x (x > 0)."""
+    import numpy as np
+    f = np.float32(x)
+    if float(f) < x:
+        f = np.nextafter(f, np.float32(np.inf))
+    return float(f)
+
+
+def sos_tables(name, spec, qnorm_abs):
+    """Float tables of the sum-of-squares form and the constants of its
+    error bound (scaled units, every |f_m| < 2):
+      beta <= beta~ (1 + (n+3) u) + TAU2 sum_i DC_i |y~_i| + K0,
+    u = 2^-24, tau = 24 u bounds |y~_i - y_i| / C_i with C_i = sum_m |L~_mi|,
+    TAU2 = 2 tau (1 + 4u), DC_i >= D~_i C_i, and K0 >= tau^2 (1 + 2u)
+    sum_i D~_i C_i^2 + 24 2^-53 |||A|||_2 4.01 n (the double-precision
+    evaluation of the printed form on the same shifted values) + 1e-30
+    (underflow)."""
+    import numpy as np
+    offs, L, D = ldl_factors(spec)
+    n = len(offs)
+    Lf = [[float(np.float32(float(L[i][j]))) for j in range(n)] for i in range(n)]
+    Df = [float(np.float32(float(d))) for d in D]
+    C = [sum(abs(Lf[m][i]) for m in range(i, n)) for i in range(n)]
+    u = 2.0 ** -24
+    tau = 24 * u
+    DC = [f32_up(Df[i] * C[i] * (1 + 4 * u)) for i in range(n)]
+    k0 = (tau ** 2 * (1 + 2 * u) * sum(Df[i] * C[i] ** 2 for i in range(n)) +
+          24 * 2.0 ** -53 * qnorm_abs * 4.01 * n + 1e-30) * 1.01
+    out = ["// %s: sum-of-squares form of the largest indicator, variables at"
+           " offsets %s" % (name, offs)]
+    out.append("static __constant__ float %s_L[%d][%d] = {" % (name, n, n))
+    for i in range(n):
+        out.append("    {" + ", ".join((float.hex(Lf[i][j]) + "f") if j <= i else "0.0f"
+                                       for j in range(n)) + "},")
+    out.append("};")
+    out.append("static __constant__ float %s_D[%d] = {" % (name, n) +
+               ", ".join(float.hex(d) + "f" for d in Df) + "};")
+    out.append("static __constant__ float %s_DC[%d] = {" % (name, n) +
+               ", ".join(float.hex(d) + "f" for d in DC) + "};")
+    out.append("#define %s_TAU2 %sf" % (name, float.hex(f32_up(2 * tau * (1 + 4 * u)))))
+    out.append("#define %s_K0 %sf" % (name, float.hex(f32_up(k0))))
+    out.append("")
+    return out
+
+
 def emit():
     import numpy as np
     out = ["// Generated by gen_coeffs.py from the integers of Eq. TENO10_AA",
@@ -111,27 +188,12 @@ def emit():
         for r in range(w):
             out.append("    {" + ", ".join(float(v).hex() if v else "0.0" for v in M[r]) + "},")
         out.append("};")
-        out.append("static __constant__ float %sF[%d][%d] = {" % (name, w, w))
-        for r in range(w):
-            out.append("    {" + ", ".join((float(np.float32(v)).hex() + "f") if v else "0.0f"
-                                           for v in M[r]) + "},")
-        out.append("};")
         out.append("")
         norms[w] = sym_norms(M, spec[1], w)
-    # small indicators in shifted values: beta0 on (s-1, s1), beta1 on (s1, s2),
-    # beta2 on (s-2, s-1)
-    small = [np.array([[4 / 3, 5 / 6], [5 / 6, 4 / 3]]),
-             np.array([[25 / 3, -19 / 6], [-19 / 6, 4 / 3]]),
-             np.array([[4 / 3, -19 / 6], [-19 / 6, 25 / 3]])]
-    sn = [(float(np.max(np.abs(np.linalg.eigvalsh(A)))) * 1.01,
-           float(np.max(np.abs(np.linalg.eigvalsh(np.abs(A))))) * 1.01) for A in small]
-    out.append("// Spectral norms (||A||, || |A| ||, rounded up) of the indicator forms on")
-    out.append("// shifted values: small stencils S0, S1, S2, then S3, S4, S5.")
-    vals = sn + [norms[6], norms[8], norms[10]]
-    out.append("static __constant__ float TENO_BNORM[6][2] = {" +
-               ", ".join("{%r, %r}" % (float(np.float32(a)), float(np.float32(b))) for a, b in vals)
-               .replace("'", "") + "};")
-    out.append("")
+    # Sum-of-squares forms of the two largest indicators (single-precision
+    # decision filter).
+    out += sos_tables("TENO_SOS8", W8, norms[8][1])
+    out += sos_tables("TENO_SOS10", W10, norms[10][1])
     return "\n".join(out)
 
 

@@ -175,7 +175,7 @@ __global__ void recon_kernel(const double *v, int64_t count, double *out, uint8_
         for (int m = 0; m < W; m++) sh[m] = vv[m] - vv[H - 1];
         uint8_t fl = 0;
         double r;
-        if (fast && fast_accept<H>(vv, sh, beta_large_s<H, H>(sh), FK, fl)) r = flux_large<H, H>(vv);
+        if (fast && fast_accept<H>(vv, sh, FK, fl)) r = flux_large<H, H>(vv);
         else r = teno_recon<H>(vv, K, fl);
         out[i] = r;
         if (flags) flags[i] = fl;
@@ -320,6 +320,7 @@ struct ProfileRecord {
     cudaEvent_t ev[2 * kMax];
     int64_t nf[kMax];
     int created = 0;
+    unsigned long long *exact = nullptr;   // device counter of exact-path reconstructions
 };
 static ProfileRecord g_prof;
 
@@ -371,6 +372,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.bc_hi = p->bc_hi[d];
         a.lam = &st->lam[d];
         a.fast = g_fast_filter;
+        a.exact_count = g_prof.on ? g_prof.exact : nullptr;
         a.FK = fastk_of(p);
         a.K = K;
         const int slot = (g_prof.on && g_prof.used < ProfileRecord::kMax) ? g_prof.used++ : -1;
@@ -610,12 +612,17 @@ int teno_set_decision_filter(int on)
 
 int teno_profile_enable(int on)
 {
+    if (on && !g_prof.exact) CUDA_TRY(cudaMalloc(&g_prof.exact, sizeof(unsigned long long)));
+    if (on) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        CUDA_TRY(cudaMemset(g_prof.exact, 0, sizeof(unsigned long long)));
+    }
     g_prof.on = on != 0;
     g_prof.used = 0;
     return TENO_OK;
 }
 
-int teno_profile_read(double *ms, int64_t *launches, int64_t *faces)
+int teno_profile_read(double *ms, int64_t *launches, int64_t *faces, int64_t *exact_recons)
 {
     double tot = 0.0;
     int64_t nf = 0;
@@ -629,6 +636,14 @@ int teno_profile_read(double *ms, int64_t *launches, int64_t *faces)
     if (ms) *ms = tot;
     if (launches) *launches = g_prof.used;
     if (faces) *faces = nf;
+    if (exact_recons) {
+        unsigned long long v = 0;
+        if (g_prof.exact) {
+            CUDA_TRY(cudaDeviceSynchronize());
+            CUDA_TRY(cudaMemcpy(&v, g_prof.exact, sizeof(v), cudaMemcpyDeviceToHost));
+        }
+        *exact_recons = (int64_t)v;
+    }
     return TENO_OK;
 }
 

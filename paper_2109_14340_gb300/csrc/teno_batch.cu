@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(TF) batch_face_kernel(
         a.bc_hi = d.bc_hi;
         a.lam = &slots[p].lam;
         a.fast = fast;
+        a.exact_count = nullptr;
         a.FK = FK;
         a.K = K;
         a.K.limiter = d.limiter;

@@ -28,6 +28,7 @@ struct FaceArgs {
     int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
+    unsigned long long *exact_count;   // adds the exact-path reconstructions, or nullptr
     FastK FK;
     Consts K;
 };
@@ -59,18 +60,38 @@ struct SmemLayout {
     static constexpr int NQ = QLR + 1;
 };
 
+// Tile shape of the 2D/3D sweeps (pencils x faces along the sweep), queue
+// capacity in reconstructions per thread, and blocks per SM the register
+// allocation is bounded for.  Measured on the 256^3 TENO10 sweep: 8 x 16
+// with three 128-thread blocks per SM (168 registers, 64 KB shared memory
+// each) beats 16 x 8 at two blocks by 9 %, and 4 x 16 / 8 x 8 at six.
+#ifndef TENO_FACE_TP
+#define TENO_FACE_TP 8
+#endif
+#ifndef TENO_FACE_TF
+#define TENO_FACE_TF 16
+#endif
+#ifndef TENO_FACE_QCAP
+#define TENO_FACE_QCAP 2
+#endif
+#ifndef TENO_FACE_MINB
+#define TENO_FACE_MINB 3
+#endif
+
 template <int ND, int H, int TP, int TF>
 constexpr size_t face_smem_bytes()
 {
     // staged cells + exact-path queue (values, owners) + per-thread results
     return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP +
-           sizeof(double) * (size_t)(2 * TP * TF) * (2 * H) +
-           sizeof(double) * (size_t)(TP * TF) * 2 * (ND + 2) + sizeof(int) * (size_t)(2 * TP * TF) +
+           sizeof(double) * (size_t)(TENO_FACE_QCAP * TP * TF) * (2 * H) +
+           sizeof(double) * (size_t)(TP * TF) * 2 * (ND + 2) +
+           sizeof(int) * (size_t)(TENO_FACE_QCAP * TP * TF) +
            (size_t)(TP * TF) * 2 * (ND + 2);
 }
 
 // One tile: faces f0 .. f0+TF-1 along D of the TP pencils starting at x0
-// (at y, z for the axes not swept).  Every thread of the block calls it; it
+// (at y, z for the axes not swept); for D = 0 the pencils run along y instead,
+// starting at y (x0 unused).  Every thread of the block calls it; it
 // synchronises once after staging and returns with no barrier pending, so a
 // persistent caller must synchronise before reusing the shared tile.
 template <int ND, int H, int D, int TP, int TF>
@@ -83,20 +104,22 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
 
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
+    const int64_t pstart = (D == 0) ? y : x0;             // first pencil
+    const int64_t npen = (D == 0) ? n1 : n0;              // pencils along that axis
     __shared__ int qcount[1];                  // exact-path queue length
     if (threadIdx.x == 0) qcount[0] = 0;
 
     // Stage cells f0-H .. f0+TF+H-2 along D.
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
         const int j = idx / TP, p = idx % TP;
-        const int64_t xg = x0 + p;
-        if (D != 0 && xg >= n0) continue;
+        const int64_t pg = pstart + p;
+        if (pg >= npen) continue;
         bool mir;
         const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, mir);
         int64_t id;
-        if (D == 0) id = gi + n0 * (y + n1 * z);
-        else if (D == 1) id = xg + n0 * (gi + n1 * z);
-        else id = xg + n0 * (y + n1 * gi);
+        if (D == 0) id = gi + n0 * (pg + n1 * z);
+        else if (D == 1) id = pg + n0 * (gi + n1 * z);
+        else id = pg + n0 * (y + n1 * gi);
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
@@ -120,12 +143,12 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 
     const int p = threadIdx.x % TP, fo = threadIdx.x / TP;
     const int64_t f = f0 + fo;
-    const bool active = !(f > nD || (D != 0 && x0 + p >= n0));
+    const bool active = !(f > nD || pstart + p >= npen);
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
 
     // Queue of reconstructions the certified filter leaves to the exact path
     // (values, owner), and per-thread result slots; after the staged cells.
-    constexpr int CAP = 2 * TP * TF;
+    constexpr int CAP = TENO_FACE_QCAP * TP * TF;
     double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
     double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]
     int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
@@ -142,9 +165,9 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         const double c2 = roe_eigensystem<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
                                                  SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
         if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
-        if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
-        else if (D == 1) flin = x0 + p + n0 * (f + (n1 + 1) * z);
-        else flin = x0 + p + n0 * (y + n1 * f);
+        if (D == 0) flin = f + (n0 + 1) * (pstart + p + n1 * z);
+        else if (D == 1) flin = pstart + p + n0 * (f + (n1 + 1) * z);
+        else flin = pstart + p + n0 * (y + n1 * f);
         // Splitting speeds over the stencil (first maximum), or at recorded cells.
         if (a.frozen_argmax) {
             const unsigned w = a.frozen_argmax[flin];
@@ -240,8 +263,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
-                const double bp = beta_large_s<H, H>(sh);
-                if (a.fast && fast_accept<H>(v, sh, bp, a.FK, fl)) {
+                if (a.fast && fast_accept<H>(v, sh, a.FK, fl)) {
                     val = flux_large<H, H>(v);
                 } else {
                     const int q = atomicAdd(&qcount[0], 1);
@@ -267,6 +289,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     if (!a.frozen) {
         __syncthreads();
         const int nq = min(qcount[0], CAP);
+        if (a.exact_count && threadIdx.x == 0 && qcount[0] > 0)
+            atomicAdd(a.exact_count, (unsigned long long)qcount[0]);
         for (int q = threadIdx.x; q < nq; q += TP * TF) {
             double v[W];
 #pragma unroll
@@ -376,11 +400,11 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 }
 
 template <int ND, int H, int D, int TP, int TF>
-__global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
+__global__ void __launch_bounds__(TP * TF, TENO_FACE_MINB) face_kernel(FaceArgs a)
 {
     extern __shared__ double sm[];
     int64_t x0 = 0, y = 0, z = 0, f0;
-    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = blockIdx.y; z = blockIdx.z; }
+    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = (int64_t)blockIdx.y * TP; z = blockIdx.z; }
     else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
     else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
     face_block<ND, H, D, TP, TF>(a, f0, x0, y, z, sm);
@@ -390,8 +414,9 @@ __global__ void __launch_bounds__(TP * TF) face_kernel(FaceArgs a)
 template <int ND, int H, int D>
 cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
 {
-    constexpr int TP = (D == 0) ? 1 : 16;
-    constexpr int TF = (D == 0) ? 128 : 8;
+    // A single line (1D) uses 1 x 128 faces.
+    constexpr int TP = (ND == 1) ? 1 : TENO_FACE_TP;
+    constexpr int TF = (ND == 1) ? 128 : TENO_FACE_TF;
     constexpr size_t smem = face_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;
     if (!attr_done) {
@@ -401,7 +426,7 @@ cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
         attr_done = true;
     }
     dim3 grid;
-    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)a.n[1], (unsigned)a.n[2]);
+    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
     else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((a.n[1] + 1 + TF - 1) / TF), (unsigned)a.n[2]);
     else grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1], (unsigned)((a.n[2] + 1 + TF - 1) / TF));
     face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);

@@ -9,12 +9,16 @@
 // answer is used; the exact FP64 path (teno_recon) decides everything else, so
 // every decision equals the FP64 evaluation of the same formulas.
 //
-// FP64 parts kept: the shifted values s_m = v_m - v_0 and the largest
-// indicator beta_p (its printed quadratic form cancels about six orders of
-// magnitude on smooth data); they are computed with exactly the operations
-// of the exact path.  FP32 parts: the three small indicators, the scale
-// separation and normalisation (all the divisions), and the first-order
-// undivided-difference measure eta -> m -> g -> [beta].
+// FP64 part kept: the shifted values s_m = v_m - v_0, computed with exactly
+// the operations of the exact path.  FP32 parts: the three small indicators,
+// the largest indicator beta_p, the scale separation and normalisation (all
+// the divisions), and the first-order undivided-difference measure eta -> m
+// -> g -> [beta].  The printed quadratic form of beta_p cancels about six
+// orders of magnitude on smooth data, so FP32 evaluates instead its exact
+// rational L D L^T factorisation, beta_p = sum_i D_i y_i^2 (a sum of
+// non-negative terms); the bound on its error includes the rounding of the
+// tables, of FP32, and of the exact path's FP64 evaluation of the printed
+// form.
 //
 // Error model: every FP32 operation is bounded by its relative rounding
 // 2^-24; conversions from FP64 truncate (relative error < 2^-23); the FP64
@@ -144,13 +148,44 @@ __device__ __forceinline__ void small_beta(float a, float ea, float b, float eb,
           beta * 1.0e-6f;
 }
 
+// Upper bound of the largest indicator beta_p (scaled units, every |f_m| < 2)
+// from the sum-of-squares form: y_i = sum_{m >= i} L_mi f_{off(m)} with the
+// variables in descending offset, off(i) = H - i for i < H and H - 1 - i
+// after; beta~ = sum_i D_i y_i^2, and
+//   beta_p <= beta~ (1 + (n+3) 2^-24) + TAU2 sum_i DC_i |y_i| + K0
+// (TAU2, DC, K0 as generated with the tables).  The final factor covers the
+// FP32 rounding of the bound itself.
+template <int H>
+__device__ __forceinline__ float beta_p_upper(const float (&f)[2 * H])
+{
+    constexpr int n = 2 * H - 1;
+    float bt = 0.0f, eb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < n; i++) {
+        const int oi = i < H ? H - i : H - 1 - i;
+        float y = f[oi + H - 1];
+#pragma unroll
+        for (int m = i + 1; m < n; m++) {
+            const int om = m < H ? H - m : H - 1 - m;
+            const float l = (H == 5) ? TENO_SOS10_L[m][i] : TENO_SOS8_L[m][i];
+            y = fmaf(l, f[om + H - 1], y);
+        }
+        const float d = (H == 5) ? TENO_SOS10_D[i] : TENO_SOS8_D[i];
+        const float dc = (H == 5) ? TENO_SOS10_DC[i] : TENO_SOS8_DC[i];
+        bt = fmaf(d, y * y, bt);
+        eb = fmaf(dc, fabsf(y), eb);
+    }
+    const float tau2 = (H == 5) ? TENO_SOS10_TAU2 : TENO_SOS8_TAU2;
+    const float k0 = (H == 5) ? TENO_SOS10_K0 : TENO_SOS8_K0;
+    return fmaf(tau2, eb, fmaf(bt, (float)(n + 3) * 5.9604645e-8f, bt) + k0) * (1.0f + 4.0e-6f);
+}
+
 // The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
-// (s[H-1] == 0); beta_p: the largest stencil's indicator as the exact path
-// computes it.  Returns true with the decision byte when "S_p accepted with
-// exponent n" is certain.
+// (s[H-1] == 0).  Returns true with the decision byte when "S_p accepted
+// with exponent n" is certain.
 template <int H>
 __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const double (&s)[2 * H],
-                                            double beta_p, const FastK &F, uint8_t &flag)
+                                            const FastK &F, uint8_t &flag)
 {
     constexpr int W = 2 * H;
 #define SV(m) s[(m) + H - 1]
@@ -256,12 +291,9 @@ __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const doub
     }
     const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;      // lower bounds (eps dropped)
     if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
-    // beta_p (FP64, exact-path value) -> scaled FP32 upper bound
-    if (!(beta_p > 0.0)) return false;
-    bool okp = true;
-    const float bp = d2f_scaled(beta_p, 2 * emax, okp);
-    if (!okp || !(bp >= tiny2)) return false;
-    const float xp = bp * (1.0f + 2.5e-7f);
+    // beta_p + eps: the upper bound, raised to tiny2 (eps < 1.3e-10 tiny2 is
+    // then inside the ratio margins).
+    const float xp = fmaxf(beta_p_upper<H>(f), tiny2);
     // chi_p >= C_T  <=>  sum_k (x_p / x_k)^7 <= 1/C_T - 1
     float tsum = 0.0f;
     {

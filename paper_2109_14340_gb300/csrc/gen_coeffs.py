@@ -176,6 +176,31 @@ def sos_tables(name, spec, qnorm_abs):
     return out
 
 
+# Optimal weights d_0, d_1, d_2 of the small stencils S0 (central), S1
+# (downwind), S2 (upwind) in the fallback of Eq. renormalize (Sec. 4.1).
+DK = ("0.5065006634", "0.3699651429", "0.1235341937")
+
+
+def fallback_table():
+    """Coefficients of the small-stencil fallback as one linear scheme on
+    offsets -2..2, for each pattern of the cut-off flags (delta_0, delta_1,
+    delta_2) = bits 0..2 of the index: w_k = d_k delta_k / sum_j d_j delta_j
+    and the 3-point candidates (Eq. reconstuction), in the operation order of
+    the device's exact path (IEEE double, no contraction)."""
+    d = [float(x) for x in DK]
+    rows = []
+    for mask in range(8):
+        dd = [d[k] if mask >> k & 1 else 0.0 for k in range(3)]
+        den = (dd[0] + dd[1]) + dd[2]
+        if den == 0.0:
+            rows.append([0.0] * 5)       # no candidate kept: cannot occur
+            continue
+        w0, w1, w2 = dd[0] / den, dd[1] / den, dd[2] / den
+        rows.append([2.0 * w2 / 6.0, (-w0 - 7.0 * w2) / 6.0, (5.0 * w0 + 2.0 * w1 + 11.0 * w2) / 6.0,
+                     (2.0 * w0 + 5.0 * w1) / 6.0, -w1 / 6.0])
+    return rows
+
+
 def emit():
     import numpy as np
     out = ["// Generated by gen_coeffs.py from the integers of Eq. TENO10_AA",
@@ -190,6 +215,14 @@ def emit():
         out.append("};")
         out.append("")
         norms[w] = sym_norms(M, spec[1], w)
+    out.append("static __constant__ double TENO_DK[3] = {%s};" % ", ".join(DK))
+    out.append("// Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,")
+    out.append("// delta_2) = bits 0..2 of the row index.")
+    out.append("static __constant__ double TENO_FBK[8][5] = {")
+    for r in fallback_table():
+        out.append("    {" + ", ".join(float.hex(x) if x else "0.0" for x in r) + "},")
+    out.append("};")
+    out.append("")
     # Sum-of-squares forms of the two largest indicators (single-precision
     # decision filter).
     out += sos_tables("TENO_SOS8", W8, norms[8][1])

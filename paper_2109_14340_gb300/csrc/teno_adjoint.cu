@@ -156,21 +156,23 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
 #define SQ(q, j, p) sm[((q) * NS + (j)) * TP + (p)]
     const double gm1 = a.K.gm1, gamma = a.K.gamma;
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
-    int64_t x0 = 0, y = 0, z = 0, f0;
-    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = blockIdx.y; z = blockIdx.z; }
-    else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
-    else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
+    // TP pencils (along x for D = 1, 2; along y for D = 0) x TF faces along D.
+    int64_t ps = 0, y = 0, z = 0, f0;
+    if (D == 0) { f0 = (int64_t)blockIdx.x * TF; ps = (int64_t)blockIdx.y * TP; z = blockIdx.z; }
+    else if (D == 1) { ps = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
+    else { ps = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
+    const int64_t npen = (D == 0) ? n1 : n0;
 
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
         const int j = idx / TP, p = idx % TP;
-        const int64_t xg = x0 + p;
-        if (D != 0 && xg >= n0) continue;
+        const int64_t pg = ps + p;
+        if (pg >= npen) continue;
         bool mir;
         const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, mir);
         int64_t id;
-        if (D == 0) id = gi + n0 * (y + n1 * z);
-        else if (D == 1) id = xg + n0 * (gi + n1 * z);
-        else id = xg + n0 * (y + n1 * gi);
+        if (D == 0) id = gi + n0 * (pg + n1 * z);
+        else if (D == 1) id = pg + n0 * (gi + n1 * z);
+        else id = pg + n0 * (y + n1 * gi);
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
@@ -196,13 +198,14 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
 
     const int p = threadIdx.x % TP, fo = threadIdx.x / TP;
     const int64_t f = f0 + fo;
-    if (f > nD || (D != 0 && x0 + p >= n0)) return;
+    if (f > nD || ps + p >= npen) return;
     const int jl = fo + H - 1, jr = fo + H;
 
     int64_t flin, cstride, cbase;      // face index; neighbouring cells along D
-    if (D == 0) { flin = f + (n0 + 1) * (y + n1 * z); cbase = n0 * (y + n1 * z); cstride = 1; }
-    else if (D == 1) { flin = x0 + p + n0 * (f + (n1 + 1) * z); cbase = x0 + p + n0 * n1 * z; cstride = n0; }
-    else { flin = x0 + p + n0 * (y + n1 * f); cbase = x0 + p + n0 * y; cstride = n0 * n1; }
+    const int64_t pg = ps + p;
+    if (D == 0) { flin = f + (n0 + 1) * (pg + n1 * z); cbase = n0 * (pg + n1 * z); cstride = 1; }
+    else if (D == 1) { flin = pg + n0 * (f + (n1 + 1) * z); cbase = pg + n0 * n1 * z; cstride = n0; }
+    else { flin = pg + n0 * (y + n1 * f); cbase = pg + n0 * y; cstride = n0 * n1; }
 
     // Adjoint of this face's flux from the adjoint of L: face f is the right
     // face of cell f-1 (-F/dx) and the left face of cell f (+F/dx).
@@ -283,28 +286,35 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
             if (k == kk) hbk = hb[kk];
         const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
         const uint8_t flp = fl[2 * k], flm = fl[2 * k + 1];
-        double hk = 0.0, wq = 0.0;
-        double Lb[nc];
+        // With P_j = (c+_j + c-_j)/2 and Q_j = (c+_j - c-_j)/2 the frozen
+        // reconstruction gives h_k = alpha sum_j Q_j w_j + sum_j P_j g_j; with
+        // A_c = sum_j Q_j U_cj and B_c = sum_j P_j F_cj (w = l.U, g = l.F):
+        // sum_j Q_j w_j = l.A, h_k = alpha l.A + l.B, and the adjoint of the
+        // row l is hb_k (alpha A + B).
+        double A[nc], B[nc];
 #pragma unroll
-        for (int c = 0; c < nc; c++) Lb[c] = 0.0;
+        for (int c = 0; c < nc; c++) { A[c] = 0.0; B[c] = 0.0; }
 #pragma unroll
         for (int j = 0; j < W; j++) {
-            double wv = lrow[0] * SQ(SL::QU, fo + j, p);
-            double gv = lrow[0] * SQ(SL::QF, fo + j, p);
-#pragma unroll
-            for (int c = 1; c < nc; c++) {
-                wv = fma(lrow[c], SQ(SL::QU + c, fo + j, p), wv);
-                gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
-            }
             const double cp = frozen_coef<H>(flp, j);          // v+ index j <-> cell j
             const double cm = frozen_coef<H>(flm, W - 1 - j);  // v- index W-1-j <-> cell j
-            hk += 0.5 * (cp * fma(alpha, wv, gv) + cm * fma(-alpha, wv, gv));
             const double Pc = 0.5 * (cp + cm), Qc = 0.5 * (cp - cm);
-            wq = fma(wv, Qc, wq);
 #pragma unroll
-            for (int c = 0; c < nc; c++)
-                Lb[c] = fma(alpha * Qc, SQ(SL::QU + c, fo + j, p), fma(Pc, SQ(SL::QF + c, fo + j, p), Lb[c]));
+            for (int c = 0; c < nc; c++) {
+                A[c] = fma(Qc, SQ(SL::QU + c, fo + j, p), A[c]);
+                B[c] = fma(Pc, SQ(SL::QF + c, fo + j, p), B[c]);
+            }
         }
+        double wq = lrow[0] * A[0], gp = lrow[0] * B[0];
+#pragma unroll
+        for (int c = 1; c < nc; c++) {
+            wq = fma(lrow[c], A[c], wq);
+            gp = fma(lrow[c], B[c], gp);
+        }
+        const double hk = fma(alpha, wq, gp);
+        double Lb[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Lb[c] = fma(alpha, A[c], B[c]);
         double ab = hbk * wq;
 #pragma unroll
         for (int kk = 0; kk < nc; kk++)
@@ -458,6 +468,15 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
     // Per stencil cell: adjoint of U (projection rows + primitive extras) and
     // of the cell's physical flux.
     double *out = a.slots + (size_t)flin * W * 2 * nc;
+    // w_j = l.U_j and g_j enter h_k with weights alpha Q_j and P_j:
+    // wb = (alpha hb_k / 2)(c+ - c-), gb = (hb_k / 2)(c+ + c-).
+    double sw[nc], sg[nc];
+#pragma unroll
+    for (int k = 0; k < nc; k++) {
+        const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
+        sg[k] = 0.5 * hb[k];
+        sw[k] = alpha * sg[k];
+    }
 #pragma unroll 1
     for (int j = 0; j < W; j++) {
         double Ub[nc], Fcb[nc];
@@ -465,11 +484,10 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         for (int c = 0; c < nc; c++) { Ub[c] = 0.0; Fcb[c] = 0.0; }
 #pragma unroll
         for (int k = 0; k < nc; k++) {
-            const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
             const double cp = frozen_coef<H>(fl[2 * k], j);
             const double cm = frozen_coef<H>(fl[2 * k + 1], W - 1 - j);
-            const double wb = alpha * (0.5 * (cp - cm)) * hb[k];
-            const double gb = 0.5 * (cp + cm) * hb[k];
+            const double wb = sw[k] * (cp - cm);
+            const double gb = sg[k] * (cp + cm);
 #pragma unroll
             for (int c = 0; c < nc; c++) {
                 Ub[c] = fma(Lm[k][c], wb, Ub[c]);
@@ -603,8 +621,8 @@ __global__ void axpby_kernel(int64_t len, double a, const double *x, double b, c
 template <int ND, int H, int D>
 cudaError_t launch_adj_direction(const AdjArgs &a, double *mu, int accumulate, cudaStream_t s)
 {
-    constexpr int TP = (D == 0) ? 1 : 32;
-    constexpr int TF = (D == 0) ? 64 : 4;
+    constexpr int TP = (ND == 1) ? 1 : 8;
+    constexpr int TF = (ND == 1) ? 64 : 16;
     constexpr size_t smem = adj_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;
     if (!attr_done) {
@@ -614,7 +632,7 @@ cudaError_t launch_adj_direction(const AdjArgs &a, double *mu, int accumulate, c
         attr_done = true;
     }
     dim3 grid;
-    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)a.n[1], (unsigned)a.n[2]);
+    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
     else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((a.n[1] + 1 + TF - 1) / TF), (unsigned)a.n[2]);
     else grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1], (unsigned)((a.n[2] + 1 + TF - 1) / TF));
     adj_face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);

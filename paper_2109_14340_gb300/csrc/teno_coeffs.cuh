@@ -35,6 +35,20 @@ static __constant__ double TENO_Q10[10][10] = {
     {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0x1.488eb1c659b24p+0},
 };
 
+static __constant__ double TENO_DK[3] = {0.5065006634, 0.3699651429, 0.1235341937};
+// Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,
+// delta_2) = bits 0..2 of the row index.
+static __constant__ double TENO_FBK[8][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {0.0, -0x1.5555555555555p-3, 0x1.aaaaaaaaaaaabp-1, 0x1.5555555555555p-2, 0.0},
+    {0.0, 0.0, 0x1.5555555555555p-2, 0x1.aaaaaaaaaaaabp-1, -0x1.5555555555555p-3},
+    {0.0, -0x1.8a8190b4b14d9p-4, 0x1.3e9b40ee6d27dp-1, 0x1.16ba1466e82dbp-1, -0x1.202919f5f95d3p-4},
+    {0x1.5555555555555p-2, -0x1.2aaaaaaaaaaabp+0, 0x1.d555555555555p+0, 0.0, 0.0},
+    {0x1.0bb53d8164a21p-4, -0x1.737298cbb6244p-2, 0x1.078750dd9833bp+0, 0x1.126805f4fc2cdp-2, 0.0},
+    {0x1.55c6337f85444p-4, -0x1.2b0d6d0f949bbp-2, 0x1.6aea27a265a10p-1, 0x1.3fdcba92d1055p-1, -0x1.ffc790eae8088p-4},
+    {0x1.5154a9140b8c8p-5, -0x1.d40cc7fd25840p-3, 0x1.8b34814102790p-1, 0x1.e896d26da89bdp-2, -0x1.f920309ce1eadp-5},
+};
+
 // TENO_SOS8: sum-of-squares form of the largest indicator, variables at offsets [4, 3, 2, 1, -1, -2, -3]
 static __constant__ float TENO_SOS8_L[7][7] = {
     {0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},

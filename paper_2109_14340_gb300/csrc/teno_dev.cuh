@@ -38,7 +38,6 @@ static __constant__ double TENO_LIN5[10] = {
     -0.2145617624175796, 0.07053731329146805, -0.01631901203296621,
     0.001832421220128962};
 // Optimal weights of the small stencils S0, S1, S2 (Sec. 4.1).
-static __constant__ double TENO_DK[3] = {0.5065006634, 0.3699651429, 0.1235341937};
 // C_T = 10^-[beta] (Eq. CT_definition), [beta] clamped to 0..22.
 static __constant__ double TENO_TENPOW[23] = {
     1e0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 1e-11,
@@ -220,19 +219,9 @@ __device__ __forceinline__ double frozen_coef(uint8_t flag, int m)
     if (sel == 3) return (off >= -4 && off <= 5) ? TENO_LIN5[off + 4] : 0.0;
     if (sel == 2) return (off >= -3 && off <= 4) ? TENO_LIN4[off + 3] : 0.0;
     if (sel == 1) return (off >= -2 && off <= 3) ? TENO_LIN3[off + 2] : 0.0;
-    const double dd0 = (flag & 4) ? TENO_DK[0] : 0.0;
-    const double dd1 = (flag & 8) ? TENO_DK[1] : 0.0;
-    const double dd2 = (flag & 16) ? TENO_DK[2] : 0.0;
-    const double den = (dd0 + dd1) + dd2;
-    const double w0 = dd0 / den, w1 = dd1 / den, w2 = dd2 / den;
-    switch (off) {
-    case -2: return 2.0 * w2 / 6.0;
-    case -1: return (-w0 - 7.0 * w2) / 6.0;
-    case 0: return (5.0 * w0 + 2.0 * w1 + 11.0 * w2) / 6.0;
-    case 1: return (2.0 * w0 + 5.0 * w1) / 6.0;
-    case 2: return -w1 / 6.0;
-    default: return 0.0;
-    }
+    // small-stencil blend with the renormalised weights (tabulated by the
+    // cut-off flags, the same double arithmetic as the exact path's weights)
+    return (off >= -2 && off <= 2) ? TENO_FBK[(flag >> 2) & 7][off + 2] : 0.0;
 }
 
 // Reconstruction with a recorded decision: the same selection as the byte

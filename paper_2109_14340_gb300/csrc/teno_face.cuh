@@ -60,32 +60,37 @@ struct SmemLayout {
     static constexpr int NQ = QLR + 1;
 };
 
-// Tile shape of the 2D/3D sweeps (pencils x faces along the sweep), queue
-// capacity in reconstructions per thread, and blocks per SM the register
-// allocation is bounded for.  Measured on the 256^3 TENO10 sweep: 8 x 16
-// with three 128-thread blocks per SM (168 registers, 64 KB shared memory
-// each) beats 16 x 8 at two blocks by 9 %, and 4 x 16 / 8 x 8 at six.
-#ifndef TENO_FACE_TP
-#define TENO_FACE_TP 8
+// Tile of the sweeps: TP pencils x TF faces along the sweep, the exact-path
+// queue's capacity in reconstructions per thread (QCAP) and the blocks per SM
+// the register allocation is bounded for (MINB).  A single line (1D) uses
+// 1 x 128.  Measured on GB300 (one 128-thread block = 8 x 16 faces):
+//   3D 256^3: three blocks per SM (168 registers, 64 KB shared memory each)
+//   beat two (at 8 x 16 or 16 x 8) by 8-9 % for TENO10 and TENO8, and
+//   4 x 16 / 8 x 8 at six; 2D 512^2 TENO8: all within 4 %, two blocks.
+// TENO_FACE_TP/TF/QCAP/MINB, when defined, override every case (tuning).
+template <int ND, int H>
+struct FaceTile {
+#ifdef TENO_FACE_TP
+    static constexpr int TP = ND == 1 ? 1 : TENO_FACE_TP;
+    static constexpr int TF = ND == 1 ? 128 : TENO_FACE_TF;
+    static constexpr int QCAP = TENO_FACE_QCAP;
+    static constexpr int MINB = TENO_FACE_MINB;
+#else
+    static constexpr int TP = ND == 1 ? 1 : 8;
+    static constexpr int TF = ND == 1 ? 128 : 16;
+    static constexpr int QCAP = 2;
+    static constexpr int MINB = ND == 3 ? 3 : 1;
 #endif
-#ifndef TENO_FACE_TF
-#define TENO_FACE_TF 16
-#endif
-#ifndef TENO_FACE_QCAP
-#define TENO_FACE_QCAP 2
-#endif
-#ifndef TENO_FACE_MINB
-#define TENO_FACE_MINB 3
-#endif
+};
 
 template <int ND, int H, int TP, int TF>
 constexpr size_t face_smem_bytes()
 {
     // staged cells + exact-path queue (values, owners) + per-thread results
     return sizeof(double) * (size_t)SmemLayout<ND>::NQ * (TF + 2 * H - 1) * TP +
-           sizeof(double) * (size_t)(TENO_FACE_QCAP * TP * TF) * (2 * H) +
+           sizeof(double) * (size_t)(FaceTile<ND, H>::QCAP * TP * TF) * (2 * H) +
            sizeof(double) * (size_t)(TP * TF) * 2 * (ND + 2) +
-           sizeof(int) * (size_t)(TENO_FACE_QCAP * TP * TF) +
+           sizeof(int) * (size_t)(FaceTile<ND, H>::QCAP * TP * TF) +
            (size_t)(TP * TF) * 2 * (ND + 2);
 }
 
@@ -148,7 +153,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 
     // Queue of reconstructions the certified filter leaves to the exact path
     // (values, owner), and per-thread result slots; after the staged cells.
-    constexpr int CAP = TENO_FACE_QCAP * TP * TF;
+    constexpr int CAP = FaceTile<ND, H>::QCAP * TP * TF;
     double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
     double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]
     int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
@@ -400,7 +405,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 }
 
 template <int ND, int H, int D, int TP, int TF>
-__global__ void __launch_bounds__(TP * TF, TENO_FACE_MINB) face_kernel(FaceArgs a)
+__global__ void __launch_bounds__(TP * TF, FaceTile<ND, H>::MINB) face_kernel(FaceArgs a)
 {
     extern __shared__ double sm[];
     int64_t x0 = 0, y = 0, z = 0, f0;
@@ -414,9 +419,8 @@ __global__ void __launch_bounds__(TP * TF, TENO_FACE_MINB) face_kernel(FaceArgs 
 template <int ND, int H, int D>
 cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
 {
-    // A single line (1D) uses 1 x 128 faces.
-    constexpr int TP = (ND == 1) ? 1 : TENO_FACE_TP;
-    constexpr int TF = (ND == 1) ? 128 : TENO_FACE_TF;
+    constexpr int TP = FaceTile<ND, H>::TP;
+    constexpr int TF = FaceTile<ND, H>::TF;
     constexpr size_t smem = face_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;
     if (!attr_done) {

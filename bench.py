@@ -487,6 +487,33 @@ def run_ours(args, rank, world, local_rank):
         t_max = float(tt.item())
     value = world * cells * args.steps / (t_max * 1e-3)
 
+    # context: the same step with every decision evaluated in FP64 (filter
+    # off), and one step from the same state both ways compared bitwise
+    Ua, Ub = U.clone(), U.clone()
+    solver.cfl_dt(Ua)
+    solver.step(Ua)
+    T.teno_set_decision_filter(False)
+    try:
+        solver.cfl_dt(Ub)
+        solver.step(Ub)
+        step()
+        torch.cuda.synchronize(dev)
+        k_off = 2
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k_off):
+            step()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_off = f0.elapsed_time(f1) / k_off
+    finally:
+        T.teno_set_decision_filter(True)
+    filter_off = {"ms_per_step": ms_off, "value": cells / (ms_off * 1e-3),
+                  "identical_step": bool(torch.equal(Ua, Ub)),
+                  "note": "same step with the single-precision decision filter off (every "
+                          "decision evaluated in FP64); outputs are identical either way"}
+    del Ua, Ub
+
     # e2e: host buffers through teno_advance_host, one step per call
     # (H2D of the state, CFL + RK3 step, D2H of the state, every step)
     Uh = U0.cpu().pin_memory()
@@ -591,6 +618,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": state_bytes + 8,
                 "call": "teno_advance_host(nsteps=1) from pinned host memory"},
         "gpu_launches": launches_per_step * args.steps,
+        "decision_filter_off": filter_off,
         "nonphysical": nonphys,
         "clocks": clk,
         "cpu_baseline": cpu,

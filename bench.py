@@ -110,21 +110,25 @@ def flops_per_face_from_flags(flags_np, nd, H):
     return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + tot_rec / nfaces, hist / nrec
 
 
+def value_flops(H, sel):
+    """FP64 flops of a reconstruction's value once its decisions are known:
+    the selected large stencil's linear scheme, or the fallback's three
+    3-point candidates and their weighted sum (weights tabulated)."""
+    return 2 * (2 * (sel + 2)) - 1 if sel else 21
+
+
 def executed_fp64_per_face(hist, exact_frac, nd, H):
     """FP64 flops the face kernel executes per face when the certified
     single-precision filter decides a fraction 1 - exact_frac of the
     reconstructions: every reconstruction forms its 2H - 1 shifted values in
-    FP64; a filtered one then evaluates only the linear scheme of the largest
-    stencil (2 (2H) - 1 flops), an exact-path one the whole method (its
-    decision mix is the measured histogram minus the filtered S_p cases).
-    The filter's own single-precision and integer work is not FP64."""
+    FP64; a decided one then evaluates only its value formula, an exact-path
+    one the whole method (both with the measured decision mix).  The
+    filter's own single-precision and integer work is not FP64."""
     nrec = 2 * (nd + 2)
     W = 2 * H
-    fast = 1.0 - exact_frac
-    per = {s: recon_flops(H, s) for s in range(4)}
-    algo = sum(hist[s] * per[s] for s in range(4))
-    exact = max(algo - fast * per[H - 2], 0.0)
-    per_rec = (W - 1) + fast * (2 * W - 1) + exact
+    algo = sum(hist[s] * recon_flops(H, s) for s in range(4))
+    val = sum(hist[s] * value_flops(H, s) for s in range(4))
+    per_rec = (W - 1) + (1.0 - exact_frac) * val + exact_frac * algo
     return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + nrec * per_rec
 
 

@@ -159,8 +159,8 @@ def sos_tables(name, spec, qnorm_abs):
     DC = [f32_up(Df[i] * C[i] * (1 + 4 * u)) for i in range(n)]
     k0 = (tau ** 2 * (1 + 2 * u) * sum(Df[i] * C[i] ** 2 for i in range(n)) +
           24 * 2.0 ** -53 * qnorm_abs * 4.01 * n + 1e-30) * 1.01
-    out = ["// %s: sum-of-squares form of the largest indicator, variables at"
-           " offsets %s" % (name, offs)]
+    out = ["// %s: sum-of-squares form of the large stencil's indicator, variables"
+           " at offsets %s" % (name, offs)]
     out.append("static __constant__ float %s_L[%d][%d] = {" % (name, n, n))
     for i in range(n):
         out.append("    {" + ", ".join((float.hex(Lf[i][j]) + "f") if j <= i else "0.0f"
@@ -179,6 +179,16 @@ def sos_tables(name, spec, qnorm_abs):
 # Optimal weights d_0, d_1, d_2 of the small stencils S0 (central), S1
 # (downwind), S2 (upwind) in the fallback of Eq. renormalize (Sec. 4.1).
 DK = ("0.5065006634", "0.3699651429", "0.1235341937")
+
+
+def fallback_weights():
+    d = [float(x) for x in DK]
+    rows = []
+    for mask in range(8):
+        dd = [d[k] if mask >> k & 1 else 0.0 for k in range(3)]
+        den = (dd[0] + dd[1]) + dd[2]
+        rows.append([x / den for x in dd] if den else [0.0, 0.0, 0.0])
+    return rows
 
 
 def fallback_table():
@@ -216,6 +226,12 @@ def emit():
         out.append("")
         norms[w] = sym_norms(M, spec[1], w)
     out.append("static __constant__ double TENO_DK[3] = {%s};" % ", ".join(DK))
+    out.append("// Renormalised fallback weights w_k = d_k delta_k / sum_j d_j delta_j (double")
+    out.append("// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index.")
+    out.append("static __constant__ double TENO_FBW[8][3] = {")
+    for r in fallback_weights():
+        out.append("    {" + ", ".join(float.hex(x) if x else "0.0" for x in r) + "},")
+    out.append("};")
     out.append("// Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,")
     out.append("// delta_2) = bits 0..2 of the row index.")
     out.append("static __constant__ double TENO_FBK[8][5] = {")
@@ -223,8 +239,9 @@ def emit():
         out.append("    {" + ", ".join(float.hex(x) if x else "0.0" for x in r) + "},")
     out.append("};")
     out.append("")
-    # Sum-of-squares forms of the two largest indicators (single-precision
+    # Sum-of-squares forms of the three large indicators (single-precision
     # decision filter).
+    out += sos_tables("TENO_SOS6", W6, norms[6][1])
     out += sos_tables("TENO_SOS8", W8, norms[8][1])
     out += sos_tables("TENO_SOS10", W10, norms[10][1])
     return "\n".join(out)

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         SQ(SL::QC, j, p) = q.c;
         SQ(SL::QH, j, p) = q.H;
         SQ(SL::QSR, j, p) = q.sr;
-        SQ(SL::QRI, j, p) = 1.0 / Uc[0];
+        SQ(SL::QRI, j, p) = q.rinv;
         const double vd = q.u[D], cj = q.c;
         SQ(SL::QLM, j, p) = fabs(vd - cj);
         SQ(SL::QL0, j, p) = fabs(vd);
@@ -245,10 +245,10 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
     for (int j = 0; j < W; j++) {
         const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
         const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
-        if (j == 0 || em > am) { am = em; jm = j; }
-        if (j == 0 || e0 > a0) { a0 = e0; j0 = j; }
-        if (j == 0 || ep > ap) { ap = ep; jp = j; }
-        if (j == 0 || er > ar) { ar = er; jrr = j; }
+        if (j == 0 || speed_gt(em, am)) { am = em; jm = j; }
+        if (j == 0 || speed_gt(e0, a0)) { a0 = e0; j0 = j; }
+        if (j == 0 || speed_gt(ep, ap)) { ap = ep; jp = j; }
+        if (j == 0 || speed_gt(er, ar)) { ar = er; jrr = j; }
     }
 
     // hb_k = sum_c R[c][k] Fb_c (adjoint of h_k = f+_k + f-_k).
@@ -291,20 +291,22 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         // A_c = sum_j Q_j U_cj and B_c = sum_j P_j F_cj (w = l.U, g = l.F):
         // sum_j Q_j w_j = l.A, h_k = alpha l.A + l.B, and the adjoint of the
         // row l is hb_k (alpha A + B).
-        double A[nc], B[nc];
+        double A[nc], B[nc];           // accumulated with 2 Q_j, 2 P_j, halved after
 #pragma unroll
         for (int c = 0; c < nc; c++) { A[c] = 0.0; B[c] = 0.0; }
 #pragma unroll
         for (int j = 0; j < W; j++) {
             const double cp = frozen_coef<H>(flp, j);          // v+ index j <-> cell j
             const double cm = frozen_coef<H>(flm, W - 1 - j);  // v- index W-1-j <-> cell j
-            const double Pc = 0.5 * (cp + cm), Qc = 0.5 * (cp - cm);
+            const double Pc = cp + cm, Qc = cp - cm;
 #pragma unroll
             for (int c = 0; c < nc; c++) {
                 A[c] = fma(Qc, SQ(SL::QU + c, fo + j, p), A[c]);
                 B[c] = fma(Pc, SQ(SL::QF + c, fo + j, p), B[c]);
             }
         }
+#pragma unroll
+        for (int c = 0; c < nc; c++) { A[c] *= 0.5; B[c] *= 0.5; }
         double wq = lrow[0] * A[0], gp = lrow[0] * B[0];
 #pragma unroll
         for (int c = 1; c < nc; c++) {

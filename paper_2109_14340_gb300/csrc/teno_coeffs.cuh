@@ -36,6 +36,18 @@ static __constant__ double TENO_Q10[10][10] = {
 };
 
 static __constant__ double TENO_DK[3] = {0.5065006634, 0.3699651429, 0.1235341937};
+// Renormalised fallback weights w_k = d_k delta_k / sum_j d_j delta_j (double
+// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index.
+static __constant__ double TENO_FBW[8][3] = {
+    {0.0, 0.0, 0.0},
+    {0x1.0000000000000p+0, 0.0, 0.0},
+    {0.0, 0x1.0000000000000p+0, 0.0},
+    {0x1.27e12c8784fa3p-1, 0x1.b03da6f0f60bcp-2, 0.0},
+    {0.0, 0.0, 0x1.0000000000000p+0},
+    {0x1.9b9c08ef7a434p-1, 0.0, 0x1.918fdc4216f32p-3},
+    {0.0, 0x1.7fd5acb02e066p-1, 0x1.0054a69fa3f33p-2},
+    {0x1.03540e11691dbp-1, 0x1.7ad82475a9702p-2, 0x1.f9fefd9e1152cp-4},
+};
 // Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,
 // delta_2) = bits 0..2 of the row index.
 static __constant__ double TENO_FBK[8][5] = {
@@ -49,7 +61,20 @@ static __constant__ double TENO_FBK[8][5] = {
     {0x1.5154a9140b8c8p-5, -0x1.d40cc7fd25840p-3, 0x1.8b34814102790p-1, 0x1.e896d26da89bdp-2, -0x1.f920309ce1eadp-5},
 };
 
-// TENO_SOS8: sum-of-squares form of the largest indicator, variables at offsets [4, 3, 2, 1, -1, -2, -3]
+// TENO_SOS6: sum-of-squares form of the large stencil's indicator, variables at offsets [3, 2, 1, -1, -2]
+static __constant__ float TENO_SOS6_L[5][5] = {
+    {0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {-0x1.47b5f20000000p+2f, 0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f},
+    {0x1.482c380000000p+3f, -0x1.dafea20000000p+1f, 0x1.0000000000000p+0f, 0.0f, 0.0f},
+    {0x1.2fa78e0000000p+2f, -0x1.70a7380000000p+1f, 0x1.99dd8e0000000p+0f, 0x1.0000000000000p+0f, 0.0f},
+    {-0x1.c2506e0000000p-1f, 0x1.3a50a00000000p-1f, -0x1.8c25b20000000p-2f, -0x1.496ec20000000p-2f, 0x1.0000000000000p+0f},
+};
+static __constant__ float TENO_SOS6_D[5] = {0x1.2785020000000p+0f, 0x1.5a97ca0000000p+0f, 0x1.0daac60000000p+1f, 0x1.07ad2c0000000p+2f, 0x1.a182be0000000p-4f};
+static __constant__ float TENO_SOS6_DC[5] = {0x1.9656ea0000000p+4f, 0x1.63784e0000000p+3f, 0x1.92de820000000p+2f, 0x1.5c811a0000000p+2f, 0x1.a182c60000000p-4f};
+#define TENO_SOS6_TAU2 0x1.8000060000000p-19f
+#define TENO_SOS6_K0 0x1.833f7e0000000p-30f
+
+// TENO_SOS8: sum-of-squares form of the large stencil's indicator, variables at offsets [4, 3, 2, 1, -1, -2, -3]
 static __constant__ float TENO_SOS8_L[7][7] = {
     {0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
     {-0x1.ca07b60000000p+2f, 0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
@@ -64,7 +89,7 @@ static __constant__ float TENO_SOS8_DC[7] = {0x1.c2220a0000000p+6f, 0x1.9783a000
 #define TENO_SOS8_TAU2 0x1.8000060000000p-19f
 #define TENO_SOS8_K0 0x1.cea02c0000000p-26f
 
-// TENO_SOS10: sum-of-squares form of the largest indicator, variables at offsets [5, 4, 3, 2, 1, -1, -2, -3, -4]
+// TENO_SOS10: sum-of-squares form of the large stencil's indicator, variables at offsets [5, 4, 3, 2, 1, -1, -2, -3, -4]
 static __constant__ float TENO_SOS10_L[9][9] = {
     {0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
     {-0x1.26131a0000000p+3f, 0x1.0000000000000p+0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},

@@ -147,6 +147,25 @@ __device__ __forceinline__ int ct_exponent(const double (&v)[2 * H], const Const
 #undef V
 }
 
+// Small-stencil fallback value (Eq. renormalize, Eq. reconstuction): the
+// kept candidates (bits 0..2 of mask) weighted by d_k renormalised over them
+// (w_k = dd_k / den, tabulated in double), the 3-point candidates divided by
+// 6 exactly as written.
+template <int H>
+__device__ __forceinline__ double fallback_value(const double (&v)[2 * H], int mask)
+{
+#define V(m) v[(m) + H - 1]
+    const double w0 = TENO_FBW[mask][0], w1 = TENO_FBW[mask][1], w2 = TENO_FBW[mask][2];
+    double f0 = ((-V(-1) + 5.0 * V(0)) + 2.0 * V(1)) / 6.0;
+    double f1 = ((2.0 * V(0) + 5.0 * V(1)) - V(2)) / 6.0;
+    double f2 = ((2.0 * V(-2) - 7.0 * V(-1)) + 11.0 * V(0)) / 6.0;
+    double fh = w0 * f0;
+    fh = fma(w1, f1, fh);
+    fh = fma(w2, f2, fh);
+    return fh;
+#undef V
+}
+
 // One reconstruction; flag: bits 0-1 selected large stencil (L-2) or 0 for the
 // small-stencil fallback, bits 2-4 deltas of S0..S2 (fallback), bits 5-7 C_T
 // exponent minus 7.
@@ -194,18 +213,23 @@ __device__ __forceinline__ double teno_recon(const double (&v)[2 * H], const Con
     // over S0, S1, S2.
     double s = g012;
     int d0 = !(g0 / s < CT), d1 = !(g1 / s < CT), d2 = !(g2 / s < CT);
-    double dd0 = d0 ? TENO_DK[0] : 0.0, dd1 = d1 ? TENO_DK[1] : 0.0, dd2 = d2 ? TENO_DK[2] : 0.0;
-    double den = (dd0 + dd1) + dd2;
-    double w0 = dd0 / den, w1 = dd1 / den, w2 = dd2 / den;
-    double f0 = ((-V(-1) + 5.0 * V(0)) + 2.0 * V(1)) / 6.0;
-    double f1 = ((2.0 * V(0) + 5.0 * V(1)) - V(2)) / 6.0;
-    double f2 = ((2.0 * V(-2) - 7.0 * V(-1)) + 11.0 * V(0)) / 6.0;
-    double fh = w0 * f0;
-    fh = fma(w1, f1, fh);
-    fh = fma(w2, f2, fh);
-    flag = (uint8_t)(((d0 | (d1 << 1) | (d2 << 2)) << 2) | fct);
-    return fh;
+    const int mask = d0 | (d1 << 1) | (d2 << 2);
+    flag = (uint8_t)((mask << 2) | fct);
+    return fallback_value<H>(v, mask);
 #undef V
+}
+
+// The value of a reconstruction whose decisions are known (decision byte in
+// the encoding above): the selected large stencil's linear scheme or the
+// small-stencil fallback, with the exact path's arithmetic.
+template <int H>
+__device__ __forceinline__ double decided_value(const double (&v)[2 * H], uint8_t flag)
+{
+    const int sel = flag & 3;
+    if (sel == H - 2) return flux_large<H, H>(v);
+    if (H == 5 && sel == 2) return flux_large<H, 4>(v);
+    if (sel == 1) return flux_large<H, 3>(v);
+    return fallback_value<H>(v, (flag >> 2) & 7);
 }
 
 // Frozen reconstruction coefficient of value index m (offset m - H + 1) for a
@@ -243,8 +267,21 @@ template <int ND>
 struct CellQ {
     double U[ND + 2], F[ND + 2];
     double u[ND];
-    double p, c, H, sr;
+    double p, c, H, sr, rinv;
 };
+
+// "e > a" for splitting speeds, which are +0, positive or NaN (absolute
+// values and |u| + c): on such doubles the order of the IEEE bit patterns
+// is the numeric order, and a NaN on either side makes the comparison false
+// exactly as the FP64 comparison does.  Integer compares keep the FP64 pipe
+// free.
+__device__ __forceinline__ bool speed_gt(double e, double a)
+{
+    const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long inf = 0x7FF0000000000000ull;
+    return eb > ab && eb <= inf && ab <= inf;
+}
 
 template <int ND, int D>
 __device__ __forceinline__ void cell_quantities(const double (&Uc)[ND + 2], const Consts &K,
@@ -255,6 +292,7 @@ __device__ __forceinline__ void cell_quantities(const double (&Uc)[ND + 2], cons
     for (int c = 0; c < nc; c++) q.U[c] = Uc[c];
     double rho = Uc[0], E = Uc[nc - 1];
     double rinv = 1.0 / rho;
+    q.rinv = rinv;
 #pragma unroll
     for (int a = 0; a < ND; a++) q.u[a] = Uc[1 + a] * rinv;
     double t = Uc[1] * q.u[0];

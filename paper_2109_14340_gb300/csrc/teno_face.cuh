@@ -111,8 +111,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
     const int64_t pstart = (D == 0) ? y : x0;             // first pencil
     const int64_t npen = (D == 0) ? n1 : n0;              // pencils along that axis
-    __shared__ int qcount[1];                  // exact-path queue length
-    if (threadIdx.x == 0) qcount[0] = 0;
+    __shared__ int qcount[2];                  // queue lengths: exact path, decided
+    if (threadIdx.x < 2) qcount[threadIdx.x] = 0;
 
     // Stage cells f0-H .. f0+TF+H-2 along D.
     for (int idx = threadIdx.x; idx < NS * TP; idx += TP * TF) {
@@ -151,9 +151,12 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     const bool active = !(f > nD || pstart + p >= npen);
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
 
-    // Queue of reconstructions the certified filter leaves to the exact path
-    // (values, owner), and per-thread result slots; after the staged cells.
-    constexpr int CAP = FaceTile<ND, H>::QCAP * TP * TF;
+    // Queue of reconstructions whose value is not computed in line (values,
+    // owner), and per-thread result slots; after the staged cells.
+    // Entries [0, QE) hold reconstructions for the exact path, [QE, CAP)
+    // decided ones whose value is not the largest stencil's scheme (its
+    // decision byte already in the owner's Qfl slot).
+    constexpr int CAP = FaceTile<ND, H>::QCAP * TP * TF, QE = CAP / 4;
     double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
     double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]
     int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
@@ -186,18 +189,21 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             for (int j = 0; j < W; j++) {
                 const double em = SQ(SL::QLM, fo + j, p), e0 = SQ(SL::QL0, fo + j, p);
                 const double ep = SQ(SL::QLP, fo + j, p), er = SQ(SL::QLR, fo + j, p);
-                if (j == 0 || em > am) { am = em; jm = j; }
-                if (j == 0 || e0 > a0) { a0 = e0; j0 = j; }
-                if (j == 0 || ep > ap) { ap = ep; jp = j; }
-                if (j == 0 || er > ar) { ar = er; jr_ = j; }
+                if (j == 0 || speed_gt(em, am)) { am = em; jm = j; }
+                if (j == 0 || speed_gt(e0, a0)) { a0 = e0; j0 = j; }
+                if (j == 0 || speed_gt(ep, ap)) { ap = ep; jp = j; }
+                if (j == 0 || speed_gt(er, ar)) { ar = er; jr_ = j; }
             }
             if (a.argmax) a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
         }
     }
 
-    // Split-flux reconstructions of every field and sign: certified ones now,
-    // the rest queued (or, if the queue is full, done in place) and drained
-    // once per tile by the whole block with the exact path.
+    // Split-flux reconstructions of every field and sign: those the filter
+    // decides for the largest stencil now, the rest queued (or, if the queue
+    // is full, done in place) and drained once per tile by the whole block --
+    // the undecided ones with the exact path, the decided ones (fallback or a
+    // smaller stencil) with their value formula, so that neither diverges
+    // inside a warp.
     double hv[2 * nc];                 // the two reconstructed values per field
 #pragma unroll
     for (int q = 0; q < 2 * nc; q++) hv[q] = 0.0;
@@ -268,18 +274,24 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
-                if (a.fast && fast_accept<H>(v, sh, a.FK, fl)) {
+                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl);
+                if (dec && (fl & 3) == H - 2) {
                     val = flux_large<H, H>(v);
                 } else {
-                    const int q = atomicAdd(&qcount[0], 1);
-                    if (q < CAP) {
+                    int q = atomicAdd(&qcount[dec ? 1 : 0], 1);
+                    const bool room = dec ? (q < CAP - QE) : (q < QE);
+                    if (room) {
+                        if (dec) {
+                            q += QE;
+                            Qfl[threadIdx.x * (2 * nc) + 2 * k + s] = fl;
+                        }
 #pragma unroll
                         for (int kk = 0; kk < W; kk++) Qv[(size_t)q * W + kk] = v[kk];
                         Qmeta[q] = (threadIdx.x << 4) | (2 * k + s);
                         pending |= 1u << (2 * k + s);
                         done = false;
-                    } else {
-                        val = teno_recon<H>(v, a.K, fl);      // queue full: in place
+                    } else {                                   // queue full: in place
+                        val = dec ? decided_value<H>(v, fl) : teno_recon<H>(v, a.K, fl);
                     }
                 }
             }
@@ -293,10 +305,10 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     }
     if (!a.frozen) {
         __syncthreads();
-        const int nq = min(qcount[0], CAP);
+        const int ne = min(qcount[0], QE), nd = min(qcount[1], CAP - QE);
         if (a.exact_count && threadIdx.x == 0 && qcount[0] > 0)
             atomicAdd(a.exact_count, (unsigned long long)qcount[0]);
-        for (int q = threadIdx.x; q < nq; q += TP * TF) {
+        for (int q = threadIdx.x; q < ne; q += TP * TF) {
             double v[W];
 #pragma unroll
             for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
@@ -305,6 +317,14 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             const int meta = Qmeta[q];
             Qres[(meta >> 4) * (2 * nc) + (meta & 15)] = r;
             Qfl[(meta >> 4) * (2 * nc) + (meta & 15)] = fl;
+        }
+        for (int q = QE + threadIdx.x; q < QE + nd; q += TP * TF) {
+            double v[W];
+#pragma unroll
+            for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
+            const int meta = Qmeta[q];
+            const int slot = (meta >> 4) * (2 * nc) + (meta & 15);
+            Qres[slot] = decided_value<H>(v, Qfl[slot]);
         }
         __syncthreads();
         if (active && pending) {

@@ -2,23 +2,26 @@
 //
 // The reconstruction's result depends on the smoothness indicators only
 // through discrete decisions: the C_T exponent [beta] of Eq. CT_definition and
-// the cut-off test chi_p >= C_T of the largest stencil (Eq. normalize, Eq.
-// cutoff).  This filter decides the common case -- "S_p is accepted, with
-// exponent n" -- in FP32 with rigorous error bounds, and says "uncertain"
-// whenever the bounds do not exclude the other outcome.  Only a certified
-// answer is used; the exact FP64 path (teno_recon) decides everything else, so
-// every decision equals the FP64 evaluation of the same formulas.
+// the cut-off tests chi >= C_T of the targeted selection (Eq. normalize, Eq.
+// cutoff, Sec. 3.3).  This filter takes every decision of one reconstruction
+// -- the exponent n, which large stencil is accepted (S_p first, then the
+// smaller ones), or, when all are rejected, the three small-stencil cut-offs
+// of the fallback -- in FP32 with rigorous error bounds, and says "uncertain"
+// whenever the bounds do not exclude another outcome.  Only a certified
+// answer is used; the exact FP64 path (teno_recon) decides everything else,
+// so every decision equals the FP64 evaluation of the same formulas, and the
+// value is then computed in FP64 with the exact path's own arithmetic.
 //
 // FP64 part kept: the shifted values s_m = v_m - v_0, computed with exactly
 // the operations of the exact path.  FP32 parts: the three small indicators,
-// the largest indicator beta_p, the scale separation and normalisation (all
+// the large-stencil indicators, the scale separation and normalisation (all
 // the divisions), and the first-order undivided-difference measure eta -> m
-// -> g -> [beta].  The printed quadratic form of beta_p cancels about six
-// orders of magnitude on smooth data, so FP32 evaluates instead its exact
-// rational L D L^T factorisation, beta_p = sum_i D_i y_i^2 (a sum of
-// non-negative terms); the bound on its error includes the rounding of the
-// tables, of FP32, and of the exact path's FP64 evaluation of the printed
-// form.
+// -> g -> [beta].  The printed quadratic forms of the large indicators
+// cancel about six orders of magnitude on smooth data, so FP32 evaluates
+// instead their exact rational L D L^T factorisations, beta = sum_i D_i y_i^2
+// (sums of non-negative terms); the bound on the error includes the rounding
+// of the tables, of FP32, and of the exact path's FP64 evaluation of the
+// printed forms.
 //
 // Error model: every FP32 operation is bounded by its relative rounding
 // 2^-24; conversions from FP64 truncate (relative error < 2^-23); the FP64
@@ -26,7 +29,9 @@
 // covered by the widening factors.  Operands are scaled by a power of two
 // (exact) so that FP32 never over- or underflows; epsilon = 1e-40 of Eq.
 // scale_separation and of the eta measure is handled by requiring the
-// indicators (in original units) to exceed 2^-100, where it is negligible.
+// indicators (in original units) to exceed 2^-100, where it is negligible,
+// and values are kept below 2^51 so that the exact path's 1/(beta+eps)^7
+// neither overflows nor underflows.
 #pragma once
 
 #include <cmath>
@@ -41,6 +46,7 @@ struct FastK {
     float alpha1, alpha2;
     int nexp_smooth;             // [beta] at m = 0, as the exact path computes it
     float thr[23];               // thr[n] <= 1 / (10^-n (1 + 2^-16)) - 1
+    float thr_rej[23];           // thr_rej[n] >= 1 / (10^-n (1 - 2^-16)) - 1
 };
 
 // Filter switch (teno_set_decision_filter), process-wide.
@@ -64,6 +70,11 @@ inline FastK fastk_make(double cr, double alpha1, double alpha2)
         float tf = (float)t;
         if ((double)tf > t) tf = nextafterf(tf, -INFINITY);
         F.thr[n] = nextafterf(tf, -INFINITY);
+        // and an upper bound of the rejection threshold
+        const double tr = 1.0 / (pow(10.0, -n) * (1.0 - 1.0 / 65536.0)) - 1.0;
+        float tu = (float)tr;
+        if ((double)tu < tr) tu = nextafterf(tu, INFINITY);
+        F.thr_rej[n] = nextafterf(tu, INFINITY);
     }
     return F;
 }
@@ -148,43 +159,86 @@ __device__ __forceinline__ void small_beta(float a, float ea, float b, float eb,
           beta * 1.0e-6f;
 }
 
-// Upper bound of the largest indicator beta_p (scaled units, every |f_m| < 2)
-// from the sum-of-squares form: y_i = sum_{m >= i} L_mi f_{off(m)} with the
-// variables in descending offset, off(i) = H - i for i < H and H - 1 - i
-// after; beta~ = sum_i D_i y_i^2, and
-//   beta_p <= beta~ (1 + (n+3) 2^-24) + TAU2 sum_i DC_i |y_i| + K0
-// (TAU2, DC, K0 as generated with the tables).  The final factor covers the
-// FP32 rounding of the bound itself.
-template <int H>
-__device__ __forceinline__ float beta_p_upper(const float (&f)[2 * H])
+// Bounds [lo, hi] of the indicator of S_L (scaled units, every |f_m| < 2)
+// from its sum-of-squares form: y_i = sum_{m >= i} L_mi f_{off(m)} with the
+// 2L - 1 variables in descending offset, off(i) = L - i for i < L and
+// L - 1 - i after; beta~ = sum_i D_i y_i^2, and
+//   |beta - beta~| <= E = (n+3) 2^-24 beta~ + TAU2 sum_i DC_i |y_i| + K0
+// (TAU2, DC, K0 as generated with the tables).  The final factors cover the
+// FP32 rounding of the bounds themselves; lo may be negative.
+template <int H, int L>
+__device__ __forceinline__ void beta_large_bounds(const float (&f)[2 * H], float &lo, float &hi)
 {
-    constexpr int n = 2 * H - 1;
+    constexpr int n = 2 * L - 1;
     float bt = 0.0f, eb = 0.0f;
 #pragma unroll
     for (int i = 0; i < n; i++) {
-        const int oi = i < H ? H - i : H - 1 - i;
+        const int oi = i < L ? L - i : L - 1 - i;
         float y = f[oi + H - 1];
 #pragma unroll
         for (int m = i + 1; m < n; m++) {
-            const int om = m < H ? H - m : H - 1 - m;
-            const float l = (H == 5) ? TENO_SOS10_L[m][i] : TENO_SOS8_L[m][i];
+            const int om = m < L ? L - m : L - 1 - m;
+            const float l = (L == 5) ? TENO_SOS10_L[m][i] : (L == 4 ? TENO_SOS8_L[m][i] : TENO_SOS6_L[m][i]);
             y = fmaf(l, f[om + H - 1], y);
         }
-        const float d = (H == 5) ? TENO_SOS10_D[i] : TENO_SOS8_D[i];
-        const float dc = (H == 5) ? TENO_SOS10_DC[i] : TENO_SOS8_DC[i];
+        const float d = (L == 5) ? TENO_SOS10_D[i] : (L == 4 ? TENO_SOS8_D[i] : TENO_SOS6_D[i]);
+        const float dc = (L == 5) ? TENO_SOS10_DC[i] : (L == 4 ? TENO_SOS8_DC[i] : TENO_SOS6_DC[i]);
         bt = fmaf(d, y * y, bt);
         eb = fmaf(dc, fabsf(y), eb);
     }
-    const float tau2 = (H == 5) ? TENO_SOS10_TAU2 : TENO_SOS8_TAU2;
-    const float k0 = (H == 5) ? TENO_SOS10_K0 : TENO_SOS8_K0;
-    return fmaf(tau2, eb, fmaf(bt, (float)(n + 3) * 5.9604645e-8f, bt) + k0) * (1.0f + 4.0e-6f);
+    const float tau2 = (L == 5) ? TENO_SOS10_TAU2 : (L == 4 ? TENO_SOS8_TAU2 : TENO_SOS6_TAU2);
+    const float k0 = (L == 5) ? TENO_SOS10_K0 : (L == 4 ? TENO_SOS8_K0 : TENO_SOS6_K0);
+    const float E = fmaf(tau2, eb, fmaf(bt, (float)(n + 3) * 5.9604645e-8f, k0));
+    hi = (bt + E) * (1.0f + 4.0e-6f);
+    lo = fmaf(-E, 1.00001f, bt) * (1.0f - 1.0e-6f);
+}
+
+// sum_k (a / b_k)^7 over three denominators, each ratio and the sum widened
+// by the relative error of the approximate division and of FP32 (up = true:
+// an upper bound of the exact sum, else a lower bound).
+__device__ __forceinline__ float pow7_sum(float a, float b0, float b1, float b2, bool up)
+{
+    const float w = up ? (1.0f + 5e-7f) : (1.0f - 5e-7f);
+    const float r0 = __fdividef(a, b0) * w, r1 = __fdividef(a, b1) * w, r2 = __fdividef(a, b2) * w;
+    const float q0 = r0 * r0, q1 = r1 * r1, q2 = r2 * r2;
+    return (q0 * q0 * q0 * r0 + q1 * q1 * q1 * r1 + q2 * q2 * q2 * r2) * (up ? (1.0f + 2e-6f) : (1.0f - 2e-6f));
+}
+
+__device__ __forceinline__ float pow7_sum2(float a, float b0, float b1, bool up)
+{
+    const float w = up ? (1.0f + 5e-7f) : (1.0f - 5e-7f);
+    const float r0 = __fdividef(a, b0) * w, r1 = __fdividef(a, b1) * w;
+    const float q0 = r0 * r0, q1 = r1 * r1;
+    return (q0 * q0 * q0 * r0 + q1 * q1 * q1 * r1) * (up ? (1.0f + 2e-6f) : (1.0f - 2e-6f));
+}
+
+// Selection among the large stencils S_L, S_(L-1), ..., S_3, largest first:
+// chi_L >= C_T  <=>  sum_k (x_L / x_k)^7 <= 1/C_T - 1.  Accept when the upper
+// bound of the sum is at most thr, reject when its lower bound exceeds
+// thr_rej; x_L = beta_L + eps with the upper bound raised to tiny2 and the
+// lower bound required to reach it.  x0..x2 / X0..X2: lower / upper bounds of
+// the small stencils' x_k.  Returns L - 2 of the accepted stencil, 0 when
+// all are rejected, -1 when uncertain.
+template <int H, int L>
+__device__ __forceinline__ int select_large(const float (&f)[2 * H], float tiny2, float x0, float x1,
+                                            float x2, float X0, float X1, float X2, float thr,
+                                            float thr_rej)
+{
+    float lo, hi;
+    beta_large_bounds<H, L>(f, lo, hi);
+    if (pow7_sum(fmaxf(hi, tiny2), x0, x1, x2, true) <= thr) return L - 2;
+    if (!(lo >= tiny2) || !(pow7_sum(lo, X0, X1, X2, false) > thr_rej)) return -1;
+    if constexpr (L > 3)
+        return select_large<H, L - 1>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+    else
+        return 0;
 }
 
 // The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
-// (s[H-1] == 0).  Returns true with the decision byte when "S_p accepted
-// with exponent n" is certain.
+// (s[H-1] == 0).  Returns true with the decision byte (the exact path's
+// encoding) when every decision is certain.
 template <int H>
-__device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const double (&s)[2 * H],
+__device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const double (&s)[2 * H],
                                             const FastK &F, uint8_t &flag)
 {
     constexpr int W = 2 * H;
@@ -204,7 +258,7 @@ __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const doub
 #pragma unroll
     for (int j = 0; j < W; j++)
         if (j != H - 1 && (__double2hiint(s[j]) & 0x7FF00000) != 0) emax = max(emax, dexp(s[j]));
-    if (emax < -900 || emax > 900) return false;
+    if (emax < -100 || emax > 50) return false;
     bool ok = true;
     float f[W];
 #pragma unroll
@@ -212,7 +266,6 @@ __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const doub
     if (!ok) return false;
     // indicator threshold 2^-100 in original units -> scaled units
     const int tb = -100 - 2 * emax;
-    if (tb > 100) return false;
     const float tiny2 = tb < -126 ? 1.17549435e-38f : __uint_as_float((unsigned)(tb + 127) << 23);
     const float u23 = 1.1920929e-7f * 1.0001f, u24 = 5.9604645e-8f * 1.0001f;
     const float z100 = 1.6e-30f;             // > 2^-100: flushed-value error
@@ -262,6 +315,8 @@ __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const doub
         if (!(b_lo == b_lo) || !(b_hi == b_hi) || n_lo != n_hi) return false;
         nexp = n_lo;
     }
+    const uint8_t fct = (uint8_t)(((nexp - 7) & 7) << 5);
+    const float thr = F.thr[nexp], thr_rej = F.thr_rej[nexp];
 
     // Small indicators on the shifted values (s_0 = 0).
     float b0, e0, b1, e1, b2, e2;
@@ -289,22 +344,35 @@ __device__ __forceinline__ bool fast_accept(const double (&v)[2 * H], const doub
         const float eb = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(b) + slack;
         small_beta(a, ea, b, eb, b2, e2);
     }
-    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;      // lower bounds (eps dropped)
+    // x_k = beta_k + eps: lower bounds (eps dropped) and upper bounds (eps
+    // < 1.3e-10 tiny2 <= 1.3e-10 x_k folded into the factor).
+    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;
     if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
-    // beta_p + eps: the upper bound, raised to tiny2 (eps < 1.3e-10 tiny2 is
-    // then inside the ratio margins).
-    const float xp = fmaxf(beta_p_upper<H>(f), tiny2);
-    // chi_p >= C_T  <=>  sum_k (x_p / x_k)^7 <= 1/C_T - 1
-    float tsum = 0.0f;
-    {
-        const float r0 = __fdividef(xp, x0) * (1.0f + 5e-7f);
-        const float r1 = __fdividef(xp, x1) * (1.0f + 5e-7f);
-        const float r2 = __fdividef(xp, x2) * (1.0f + 5e-7f);
-        const float q0 = r0 * r0, q1 = r1 * r1, q2 = r2 * r2;
-        tsum = (q0 * q0 * q0 * r0 + q1 * q1 * q1 * r1 + q2 * q2 * q2 * r2) * (1.0f + 2e-6f);
+    const float X0 = (b0 + e0) * (1.0f + 1e-6f), X1 = (b1 + e1) * (1.0f + 1e-6f);
+    const float X2 = (b2 + e2) * (1.0f + 1e-6f);
+
+    // Targeted selection, largest group first (Sec. 3.3).
+    const int sel = select_large<H, H>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+    if (sel < 0) return false;
+    if (sel > 0) {
+        flag = (uint8_t)(sel | fct);
+        return true;
     }
-    if (!(tsum <= F.thr[nexp])) return false;
-    flag = (uint8_t)((H - 2) | (((nexp - 7) & 7) << 5));
+
+    // Small-stencil fallback (Eq. renormalize): delta_k = !(g_k / sum < C_T),
+    // g_k / sum >= C_T  <=>  sum_{j != k} (x_k / x_j)^7 <= 1/C_T - 1.
+    int d[3];
+    {
+        const float xl[3] = {x0, x1, x2}, xu[3] = {X0, X1, X2};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+            if (pow7_sum2(xu[k], xl[j1], xl[j2], true) <= thr) d[k] = 1;
+            else if (pow7_sum2(xl[k], xu[j1], xu[j2], false) > thr_rej) d[k] = 0;
+            else return false;
+        }
+    }
+    flag = (uint8_t)(((d[0] | (d[1] << 1) | (d[2] << 2)) << 2) | fct);
     return true;
 #undef FF
 #undef SV

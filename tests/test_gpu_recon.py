@@ -107,6 +107,23 @@ def adversarial(scheme):
         if r:
             for x in neighbours(r[0]) + neighbours(r[1]):
                 out.append(make2(x))
+    # every decision bit (which large stencil, the small-stencil cut-offs of
+    # the fallback, the exponent): steps and kinks at each stencil position
+    # scanned in amplitude, each change of the decision byte bisected
+    key_all = lambda v: oracle.recon(po, v)[1]
+    base = np.sin(0.4 * offs) + 3.0
+    for q in offs[1:]:
+        fams = (lambda t, q=q: base + t * (offs >= q),
+                lambda t, q=q: base + t * np.maximum(offs - q + 1, 0.0))
+        for make3 in fams:
+            ts = np.concatenate([[0.0], np.geomspace(1e-4, 50.0, 48)])
+            ks = [key_all(make3(t)) for t in ts]
+            for i in range(1, len(ts)):
+                if ks[i] != ks[i - 1]:
+                    r = bisect(make3, ts[i - 1], ts[i], key_all)
+                    if r:
+                        for x in neighbours(r[0], 2) + neighbours(r[1], 2):
+                            out.append(make3(x))
     return np.array(out)
 
 
@@ -116,7 +133,7 @@ def random_stencils(scheme, n=20000, seed=7):
     offs = np.arange(W, dtype=float)
     V = []
     for i in range(n):
-        kind = i % 6
+        kind = i % 8
         scale = 10.0 ** g.uniform(-8, 8)
         shift = g.uniform(-1, 1) * 10.0 ** g.uniform(-2, 6)
         if kind == 0:      # smooth
@@ -127,6 +144,10 @@ def random_stencils(scheme, n=20000, seed=7):
             v = (offs >= g.integers(0, W)).astype(float) * scale + shift + 1e-3 * scale * np.sin(offs)
         elif kind == 3:    # near-constant: rounding-level variation
             v = shift + 1.0 + np.abs(shift) * 1e-15 * g.standard_normal(W)
+        elif kind == 6:    # magnitudes where 1/(beta+eps)^7 leaves the double range
+            v = g.standard_normal(W) * 10.0 ** g.uniform(20, 80) + shift
+        elif kind == 7:    # tiny values: indicators near eps
+            v = g.standard_normal(W) * 10.0 ** g.uniform(-80, -15)
         elif kind == 4:    # ghost-like: constant run then smooth
             k = g.integers(1, W)
             v = np.sin(0.2 * offs) * scale + shift
@@ -157,3 +178,6 @@ def test_adversarial_families_reach_both_sides(scheme):
     assert len(V) > 50
     assert len(set((rfl & 3).tolist())) >= 2
     assert len(set(((rfl >> 5) & 7).tolist())) >= 5
+    # every selectable large stencil, and fallbacks with different cut-offs
+    assert set(range(1, scheme // 2 - 1)) <= set((rfl & 3).tolist())
+    assert len(set(((rfl >> 2) & 7)[(rfl & 3) == 0].tolist())) >= 3

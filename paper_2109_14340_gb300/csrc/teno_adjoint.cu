@@ -41,7 +41,8 @@ struct AdjSmem {
     static constexpr int nc = ND + 2;
     static constexpr int QU = 0, QF = nc, QV = 2 * nc;
     static constexpr int QP = QV + ND, QC = QP + 1, QH = QP + 2, QSR = QP + 3, QRI = QP + 4;
-    static constexpr int QLM = QP + 5, QL0 = QLM + 1, QLP = QLM + 2, QLR = QLM + 3;
+    static constexpr int QCI = QP + 5;                  // 1 / c
+    static constexpr int QLM = QP + 6, QL0 = QLM + 1, QLP = QLM + 2, QLR = QLM + 3;
     static constexpr int NQ = QLR + 1;
 };
 
@@ -52,10 +53,11 @@ constexpr size_t adj_smem_bytes()
 }
 
 // Reverse of cell_quantities for the primitive outputs: adjoints of the
-// velocity ub, sound speed cb, enthalpy Hb and sqrt(rho) sb -> adjoint of U.
+// velocity ub, sound speed cb, enthalpy Hb and sqrt(rho) sb -> adjoint of U
+// (added into Ub); cinv = 1/c and rinv = 1/rho as staged.
 template <int ND>
 __device__ __forceinline__ void prim_adjoint(const double (&Uc)[ND + 2], const double (&u)[ND],
-                                             double p, double c, double sr, double rinv,
+                                             double p, double cinv, double sr, double rinv,
                                              const double (&ub_in)[ND], double cb, double Hb,
                                              double sb, double gamma, double gm1,
                                              double (&Ub)[ND + 2])
@@ -69,11 +71,11 @@ __device__ __forceinline__ void prim_adjoint(const double (&Uc)[ND + 2], const d
     double rb = 0.0, Eb = 0.0, mb[ND];
 #pragma unroll
     for (int a = 0; a < ND; a++) mb[a] = 0.0;
-    rb += sb * 0.5 / sr;                         // sr = sqrt(rho)
+    rb += sb * 0.5 * (sr * rinv);                // sr = sqrt(rho): 1/sr = sr rinv
     double Epb = Hb * rinv, rinvb = Hb * Ep;     // H = Ep rinv
     Eb += Epb;                                   // Ep = E + p
     double pb = Epb;
-    const double zb = cb * 0.5 / c;              // c = sqrt(gamma p rinv)
+    const double zb = cb * 0.5 * cinv;           // c = sqrt(gamma p rinv)
     pb += gamma * rinv * zb;
     rinvb += gamma * p * zb;
     Eb += gm1 * pb;                              // p = gm1 (E - ke)
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         SQ(SL::QH, j, p) = q.H;
         SQ(SL::QSR, j, p) = q.sr;
         SQ(SL::QRI, j, p) = q.rinv;
+        SQ(SL::QCI, j, p) = 1.0 / q.c;
         const double vd = q.u[D], cj = q.c;
         SQ(SL::QLM, j, p) = fabs(vd - cj);
         SQ(SL::QL0, j, p) = fabs(vd);
@@ -224,18 +227,13 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
     const double Hl = SQ(SL::QH, jl, p), Hr = SQ(SL::QH, jr, p);
     const double sl = SQ(SL::QSR, jl, p), srr = SQ(SL::QSR, jr, p);
     double Lm[nc][nc], Rm[nc][nc];
-    roe_eigensystem<ND, D>(ul, Hl, sl, ur, Hr, srr, gm1, Lm, Rm);
-    const double inv = 1.0 / (sl + srr);
+    RoeScalars<ND> rs;
+    roe_eigensystem<ND, D>(ul, Hl, sl, ur, Hr, srr, gm1, Lm, Rm, &rs);
+    const double inv = rs.inv;
     double ut[ND];
 #pragma unroll
-    for (int k = 0; k < ND; k++) ut[k] = fma(srr, ur[k], sl * ul[k]) * inv;
-    const double Ht = fma(srr, Hr, sl * Hl) * inv;
-    double q2 = ut[0] * ut[0];
-#pragma unroll
-    for (int k = 1; k < ND; k++) q2 = fma(ut[k], ut[k], q2);
-    const double ct = sqrt(gm1 * (Ht - 0.5 * q2));
-    const double cinv = 1.0 / ct;
-    const double b1 = gm1 * (cinv * cinv);
+    for (int k = 0; k < ND; k++) ut[k] = rs.ut[k];
+    const double Ht = rs.Ht, q2 = rs.q2, ct = rs.ct, cinv = rs.cinv, b1 = rs.b1;
     const double un = ut[D];
 
     // Splitting speeds and their maximising cells (first maximum, as forward).
@@ -467,8 +465,8 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         cb_p = sp_ * alphab[last];
     }
 
-    // Per stencil cell: adjoint of U (projection rows + primitive extras) and
-    // of the cell's physical flux.
+    // Per stencil cell: adjoint of U through the projection rows, and of the
+    // cell's physical flux (the primitive-variable parts follow).
     double *out = a.slots + (size_t)flin * W * 2 * nc;
     // w_j = l.U_j and g_j enter h_k with weights alpha Q_j and P_j:
     // wb = (alpha hb_k / 2)(c+ - c-), gb = (hb_k / 2)(c+ + c-).
@@ -496,46 +494,55 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
                 Fcb[c] = fma(Lm[k][c], gb, Fcb[c]);
             }
         }
-        double ue[ND], ce = 0.0, He = 0.0, se = 0.0;
-        bool any = false;
-#pragma unroll
-        for (int aa = 0; aa < ND; aa++) ue[aa] = 0.0;
-        if (j == H - 1) {                        // cell i of the Roe average
-#pragma unroll
-            for (int aa = 0; aa < ND; aa++) ue[aa] += ulb[aa];
-            He += Hlb;
-            se += slb;
-            any = true;
-        }
-        if (j == H) {                            // cell i+1
-#pragma unroll
-            for (int aa = 0; aa < ND; aa++) ue[aa] += urb[aa];
-            He += Hrb;
-            se += srb;
-            any = true;
-        }
-        if (a.K.split) {
-            if (j == jrr) { ue[D] += udb_r; ce += cb_r; any = true; }
-        } else {
-            if (j == jm) { ue[D] += udb_m; ce += cb_m; any = true; }
-            if (j == j0) { ue[D] += udb_0; any = true; }
-            if (j == jp) { ue[D] += udb_p; ce += cb_p; any = true; }
-        }
-        if (any) {
-            double Uc[nc], u[ND];
-#pragma unroll
-            for (int c = 0; c < nc; c++) Uc[c] = SQ(SL::QU + c, fo + j, p);
-#pragma unroll
-            for (int aa = 0; aa < ND; aa++) u[aa] = SQ(SL::QV + aa, fo + j, p);
-            prim_adjoint<ND>(Uc, u, SQ(SL::QP, fo + j, p), SQ(SL::QC, fo + j, p),
-                             SQ(SL::QSR, fo + j, p), SQ(SL::QRI, fo + j, p), ue, ce, He, se,
-                             gamma, gm1, Ub);
-        }
 #pragma unroll
         for (int c = 0; c < nc; c++) {
             out[j * 2 * nc + c] = Ub[c];
             out[j * 2 * nc + nc + c] = Fcb[c];
         }
+    }
+
+    // Primitive-variable parts, one contribution at a time (the same number
+    // for every face, so no lane waits on another's): the Roe state's cells
+    // i and i+1, and the splitting speeds at their maximising cells.  Each is
+    // added into the slot written above.
+#pragma unroll
+    for (int e = 0; e < 5; e++) {
+        if (a.K.split && e > 2) continue;
+        int je;
+        double ue[ND], ce = 0.0, He = 0.0, se = 0.0;
+#pragma unroll
+        for (int aa = 0; aa < ND; aa++) ue[aa] = 0.0;
+        if (e == 0) {                            // cell i of the Roe average
+            je = H - 1;
+#pragma unroll
+            for (int aa = 0; aa < ND; aa++) ue[aa] = ulb[aa];
+            He = Hlb;
+            se = slb;
+        } else if (e == 1) {                     // cell i+1
+            je = H;
+#pragma unroll
+            for (int aa = 0; aa < ND; aa++) ue[aa] = urb[aa];
+            He = Hrb;
+            se = srb;
+        } else if (a.K.split) {
+            je = jrr; ue[D] = udb_r; ce = cb_r;
+        } else if (e == 2) {
+            je = jm; ue[D] = udb_m; ce = cb_m;
+        } else if (e == 3) {
+            je = j0; ue[D] = udb_0;
+        } else {
+            je = jp; ue[D] = udb_p; ce = cb_p;
+        }
+        double Uc[nc], u[ND], Ub[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) { Uc[c] = SQ(SL::QU + c, fo + je, p); Ub[c] = 0.0; }
+#pragma unroll
+        for (int aa = 0; aa < ND; aa++) u[aa] = SQ(SL::QV + aa, fo + je, p);
+        prim_adjoint<ND>(Uc, u, SQ(SL::QP, fo + je, p), SQ(SL::QCI, fo + je, p),
+                         SQ(SL::QSR, fo + je, p), SQ(SL::QRI, fo + je, p), ue, ce, He, se,
+                         gamma, gm1, Ub);
+#pragma unroll
+        for (int c = 0; c < nc; c++) out[je * 2 * nc + c] += Ub[c];
     }
 #undef SQ
 }

@@ -329,11 +329,18 @@ __device__ __forceinline__ double pressure_of(const double (&Uc)[ND + 2], double
 // Roe average (Sec. 5) and eigenvectors of dF_D/dU.  Field order: u-c,
 // entropy, shear waves (tangential axes ascending), u+c.
 // ---------------------------------------------------------------------------
+// The Roe state's scalars, as roe_eigensystem computes them.
+template <int ND>
+struct RoeScalars {
+    double ut[ND], Ht, q2, ct, cinv, b1, inv;   // inv = 1 / (sqrt(rho_l) + sqrt(rho_r))
+};
+
 template <int ND, int D>
 __device__ __forceinline__ double roe_eigensystem(const double (&ul)[ND], double Hl, double sl,
                                                   const double (&ur)[ND], double Hr, double sr,
                                                   double gm1, double (&Lm)[ND + 2][ND + 2],
-                                                  double (&Rm)[ND + 2][ND + 2])
+                                                  double (&Rm)[ND + 2][ND + 2],
+                                                  RoeScalars<ND> *rs = nullptr)
 {
     constexpr int nc = ND + 2, last = nc - 1;
     double inv = 1.0 / (sl + sr);
@@ -394,6 +401,16 @@ __device__ __forceinline__ double roe_eigensystem(const double (&ul)[ND], double
         Rm[1 + a][k] = 1.0;
         Rm[last][k] = ut[a];
         k++;
+    }
+    if (rs) {
+#pragma unroll
+        for (int a = 0; a < ND; a++) rs->ut[a] = ut[a];
+        rs->Ht = Ht;
+        rs->q2 = q2;
+        rs->ct = ct;
+        rs->cinv = cinv;
+        rs->b1 = b1;
+        rs->inv = inv;
     }
     return c2;
 }

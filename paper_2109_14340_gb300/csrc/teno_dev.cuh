@@ -329,89 +329,125 @@ __device__ __forceinline__ double pressure_of(const double (&Uc)[ND + 2], double
 // Roe average (Sec. 5) and eigenvectors of dF_D/dU.  Field order: u-c,
 // entropy, shear waves (tangential axes ascending), u+c.
 // ---------------------------------------------------------------------------
-// The Roe state's scalars, as roe_eigensystem computes them.
+// The Roe state's scalars; every eigenvector entry is one expression of
+// them (l_row, r_entry), so kernels may keep these instead of the matrices.
 template <int ND>
 struct RoeScalars {
-    double ut[ND], Ht, q2, ct, cinv, b1, inv;   // inv = 1 / (sqrt(rho_l) + sqrt(rho_r))
+    double ut[ND], Ht, q2, ct, cinv, b1, b2, unc, bu, unct;
+    double inv;                        // 1 / (sqrt(rho_l) + sqrt(rho_r))
 };
+
+// Roe average of two cells (velocities, enthalpies, sqrt(rho)); returns
+// c~^2 (the caller counts c~^2 <= 0 as non-physical).
+template <int ND, int D>
+__device__ __forceinline__ double roe_state(const double (&ul)[ND], double Hl, double sl,
+                                            const double (&ur)[ND], double Hr, double sr,
+                                            double gm1, RoeScalars<ND> &rs)
+{
+    const double inv = 1.0 / (sl + sr);
+#pragma unroll
+    for (int a = 0; a < ND; a++) rs.ut[a] = fma(sr, ur[a], sl * ul[a]) * inv;
+    rs.Ht = fma(sr, Hr, sl * Hl) * inv;
+    double q2 = rs.ut[0] * rs.ut[0];
+#pragma unroll
+    for (int a = 1; a < ND; a++) q2 = fma(rs.ut[a], rs.ut[a], q2);
+    rs.q2 = q2;
+    const double c2 = gm1 * (rs.Ht - 0.5 * q2);
+    rs.ct = sqrt(c2);
+    rs.cinv = 1.0 / rs.ct;
+    rs.b1 = gm1 * (rs.cinv * rs.cinv);
+    rs.b2 = (0.5 * q2) * rs.b1;
+    const double un = rs.ut[D];
+    rs.unc = un * rs.cinv;
+    rs.bu = rs.b1 * un;
+    rs.unct = un * rs.ct;
+    rs.inv = inv;
+    return c2;
+}
+
+// Tangential axis of shear field k (2 <= k < ND + 1), ascending.
+template <int ND, int D>
+__device__ __forceinline__ int shear_axis(int k)
+{
+    int t = 0, kk = 2;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        if (a == D) continue;
+        if (kk == k) t = a;
+        kk++;
+    }
+    return t;
+}
+
+// Row k of L = R^-1 (b1 = (gamma-1)/c^2, b2 = |u|^2 b1 / 2).
+template <int ND, int D>
+__device__ __forceinline__ void l_row(const RoeScalars<ND> &rs, int k, double (&l)[ND + 2])
+{
+    constexpr int last = ND + 1;
+    if (k == 0 || k == last) {
+        const bool m = (k == 0);
+        l[0] = 0.5 * (m ? rs.b2 + rs.unc : rs.b2 - rs.unc);
+#pragma unroll
+        for (int a = 0; a < ND; a++) {
+            if (a == D) l[1 + a] = 0.5 * (m ? -rs.bu - rs.cinv : rs.cinv - rs.bu);
+            else l[1 + a] = 0.5 * (-(rs.b1 * rs.ut[a]));
+        }
+        l[last] = 0.5 * rs.b1;
+    } else if (k == 1) {
+        l[0] = 1.0 - rs.b2;
+#pragma unroll
+        for (int a = 0; a < ND; a++) l[1 + a] = rs.b1 * rs.ut[a];
+        l[last] = -rs.b1;
+    } else {
+        const int t = shear_axis<ND, D>(k);
+        l[0] = -rs.ut[t];
+#pragma unroll
+        for (int a = 0; a < ND; a++) l[1 + a] = (a == t) ? 1.0 : 0.0;
+        l[last] = 0.0;
+    }
+}
+
+// Entry (row c, column k) of R: columns (1, u - c e_D, H - u_D c),
+// (1, u, |u|^2/2), shear (0, e_t, u_t), (1, u + c e_D, H + u_D c).
+template <int ND, int D>
+__device__ __forceinline__ double r_entry(const RoeScalars<ND> &rs, int c, int k)
+{
+    constexpr int last = ND + 1;
+    const double un = rs.ut[D];
+    if (k == 0 || k == 1 || k == last) {
+        if (c == 0) return 1.0;
+        if (c == last) return k == 0 ? rs.Ht - rs.unct : (k == 1 ? 0.5 * rs.q2 : rs.Ht + rs.unct);
+        const int a = c - 1;
+        if (a == D && k == 0) return un - rs.ct;
+        if (a == D && k == last) return un + rs.ct;
+        return rs.ut[a];
+    }
+    const int t = shear_axis<ND, D>(k);
+    if (c == last) return rs.ut[t];
+    return (c == 1 + t) ? 1.0 : 0.0;
+}
 
 template <int ND, int D>
 __device__ __forceinline__ double roe_eigensystem(const double (&ul)[ND], double Hl, double sl,
                                                   const double (&ur)[ND], double Hr, double sr,
                                                   double gm1, double (&Lm)[ND + 2][ND + 2],
                                                   double (&Rm)[ND + 2][ND + 2],
-                                                  RoeScalars<ND> *rs = nullptr)
+                                                  RoeScalars<ND> *rsp = nullptr)
 {
-    constexpr int nc = ND + 2, last = nc - 1;
-    double inv = 1.0 / (sl + sr);
-    double ut[ND];
+    constexpr int nc = ND + 2;
+    RoeScalars<ND> rs;
+    const double c2 = roe_state<ND, D>(ul, Hl, sl, ur, Hr, sr, gm1, rs);
 #pragma unroll
-    for (int a = 0; a < ND; a++) ut[a] = fma(sr, ur[a], sl * ul[a]) * inv;
-    double Ht = fma(sr, Hr, sl * Hl) * inv;
-    double q2 = ut[0] * ut[0];
+    for (int k = 0; k < nc; k++) {
+        double l[nc];
+        l_row<ND, D>(rs, k, l);
 #pragma unroll
-    for (int a = 1; a < ND; a++) q2 = fma(ut[a], ut[a], q2);
-    double c2 = gm1 * (Ht - 0.5 * q2);
-    double ct = sqrt(c2);
-    double cinv = 1.0 / ct;
-    double b1 = gm1 * (cinv * cinv);
-    double b2 = (0.5 * q2) * b1;
-    double un = ut[D];
-    double unc = un * cinv;
-    double bu = b1 * un;
-    double unct = un * ct;
-#pragma unroll
-    for (int r = 0; r < nc; r++)
-#pragma unroll
-        for (int c = 0; c < nc; c++) { Lm[r][c] = 0.0; Rm[r][c] = 0.0; }
-    Lm[0][0] = 0.5 * (b2 + unc);
-    Lm[last][0] = 0.5 * (b2 - unc);
-    Lm[1][0] = 1.0 - b2;
-#pragma unroll
-    for (int a = 0; a < ND; a++) {
-        double ba = b1 * ut[a];
-        if (a == D) {
-            Lm[0][1 + a] = 0.5 * (-bu - cinv);
-            Lm[last][1 + a] = 0.5 * (cinv - bu);
-        } else {
-            Lm[0][1 + a] = 0.5 * (-ba);
-            Lm[last][1 + a] = 0.5 * (-ba);
+        for (int c = 0; c < nc; c++) {
+            Lm[k][c] = l[c];
+            Rm[c][k] = r_entry<ND, D>(rs, c, k);
         }
-        Lm[1][1 + a] = ba;
     }
-    Lm[0][last] = 0.5 * b1;
-    Lm[last][last] = 0.5 * b1;
-    Lm[1][last] = -b1;
-    Rm[0][0] = 1.0; Rm[0][1] = 1.0; Rm[0][last] = 1.0;
-#pragma unroll
-    for (int a = 0; a < ND; a++) {
-        Rm[1 + a][0] = (a == D) ? un - ct : ut[a];
-        Rm[1 + a][1] = ut[a];
-        Rm[1 + a][last] = (a == D) ? un + ct : ut[a];
-    }
-    Rm[last][0] = Ht - unct;
-    Rm[last][1] = 0.5 * q2;
-    Rm[last][last] = Ht + unct;
-    int k = 2;
-#pragma unroll
-    for (int a = 0; a < ND; a++) {
-        if (a == D) continue;
-        Lm[k][0] = -ut[a];
-        Lm[k][1 + a] = 1.0;
-        Rm[1 + a][k] = 1.0;
-        Rm[last][k] = ut[a];
-        k++;
-    }
-    if (rs) {
-#pragma unroll
-        for (int a = 0; a < ND; a++) rs->ut[a] = ut[a];
-        rs->Ht = Ht;
-        rs->q2 = q2;
-        rs->ct = ct;
-        rs->cinv = cinv;
-        rs->b1 = b1;
-        rs->inv = inv;
-    }
+    if (rsp) *rsp = rs;
     return c2;
 }
 

@@ -162,7 +162,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
     uint8_t *Qfl = (uint8_t *)(Qmeta + CAP);          // [threads][2 nc]
 
-    double Lm[nc][nc], Rm[nc][nc];
+    RoeScalars<ND> rs;                 // eigenvector rows / columns are built from these
     double am = 0.0, a0 = 0.0, ap = 0.0, ar = 0.0;
     int64_t flin = 0;
     if (active) {
@@ -170,8 +170,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         double ul[ND], ur[ND];
 #pragma unroll
         for (int k = 0; k < ND; k++) { ul[k] = SQ(SL::QV + k, jl, p); ur[k] = SQ(SL::QV + k, jr, p); }
-        const double c2 = roe_eigensystem<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
-                                                 SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, Lm, Rm);
+        const double c2 = roe_state<ND, D>(ul, SQ(SL::QH, jl, p), SQ(SL::QSR, jl, p), ur,
+                                           SQ(SL::QH, jr, p), SQ(SL::QSR, jr, p), a.K.gm1, rs);
         if (!(c2 > 0.0)) atomicAdd(&a.st->nonphys, 1ull);
         if (D == 0) flin = f + (n0 + 1) * (pstart + p + n1 * z);
         else if (D == 1) flin = pstart + p + n0 * (f + (n1 + 1) * z);
@@ -212,25 +212,9 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     for (int k = 0; k < nc; k++) {
         if (!active) break;
         const bool shear = (k >= 2 && k < last);
-        int tax = 0;
-        {
-            int kk = 2;
-#pragma unroll
-            for (int aa = 0; aa < ND; aa++) {
-                if (aa == D) continue;
-                if (kk == k) tax = aa;
-                kk++;
-            }
-        }
+        const int tax = shear ? shear_axis<ND, D>(k) : 0;
         double lrow[nc];
-#pragma unroll
-        for (int c = 0; c < nc; c++) {
-            double lv = Lm[0][c];
-#pragma unroll
-            for (int kk = 1; kk < nc; kk++)
-                if (k == kk) lv = Lm[kk][c];
-            lrow[c] = lv;
-        }
+        l_row<ND, D>(rs, k, lrow);
         const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
         const double ha = 0.5 * alpha;
         double w[W], hg[W];
@@ -347,7 +331,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             const double hsum = hv[2 * k] + hv[2 * k + 1];
             if (k == 0) {
 #pragma unroll
-                for (int c = 0; c < nc; c++) Fo[c] = Rm[c][0] * hsum;
+                for (int c = 0; c < nc; c++) Fo[c] = r_entry<ND, D>(rs, c, 0) * hsum;
             } else if (k >= 2 && k < last) {
                 int tax = 0, kk = 2;
 #pragma unroll
@@ -357,10 +341,10 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                     kk++;
                 }
                 Fo[1 + tax] = Fo[1 + tax] + hsum;
-                Fo[last] = fma(Rm[last][k], hsum, Fo[last]);
+                Fo[last] = fma(r_entry<ND, D>(rs, last, k), hsum, Fo[last]);
             } else {
 #pragma unroll
-                for (int c = 0; c < nc; c++) Fo[c] = fma(Rm[c][k], hsum, Fo[c]);
+                for (int c = 0; c < nc; c++) Fo[c] = fma(r_entry<ND, D>(rs, c, k), hsum, Fo[c]);
             }
         }
     }

@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(TP * TF, FaceTile<ND, H>::MINB) face_kernel(Fa
     int64_t x0 = 0, y = 0, z = 0, f0;
     if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = (int64_t)blockIdx.y * TP; z = blockIdx.z; }
     else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
-    else { x0 = (int64_t)blockIdx.x * TP; y = blockIdx.y; f0 = (int64_t)blockIdx.z * TF; }
+    else { f0 = (int64_t)blockIdx.x * TF; x0 = (int64_t)blockIdx.y * TP; y = blockIdx.z; }
     face_block<ND, H, D, TP, TF>(a, f0, x0, y, z, sm);
 }
 
@@ -436,7 +436,8 @@ cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
     dim3 grid;
     if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
     else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((a.n[1] + 1 + TF - 1) / TF), (unsigned)a.n[2]);
-    else grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1], (unsigned)((a.n[2] + 1 + TF - 1) / TF));
+    else   // z tiles fastest: consecutive blocks share their halo planes through L2
+        grid = dim3((unsigned)((a.n[2] + 1 + TF - 1) / TF), (unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1]);
     face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);
     return cudaGetLastError();
 }

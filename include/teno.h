@@ -60,7 +60,9 @@ typedef struct teno_params {
     int32_t scheme;        /* 8 (TENO8-AA, Sec. 4.3) or 10 (TENO10-AA, Sec. 4.2) */
     int32_t flux_split;    /* TENO_SPLIT_LLF or TENO_SPLIT_RUSANOV              */
     int32_t limiter;       /* 1: positivity-preserving flux limiter (Sec. 5.3)  */
-    int64_t n[3];          /* interior cells per axis, x fastest; 1 if unused   */
+    int64_t n[3];          /* interior cells per axis, x fastest; 1 if unused;
+                              H <= n[d] <= 2^31 on used axes (H = scheme / 2)
+                              and n[1], n[2] <= 65535 (CUDA grid limits)    */
     double dx[3];          /* uniform spacing per axis (> 0)                    */
     double gamma;          /* ratio of specific heats (> 1), ideal-gas EOS      */
     double ct_alpha1;      /* alpha_1 of Eq. CT_definition, default 14          */

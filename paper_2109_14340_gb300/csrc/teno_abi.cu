@@ -38,48 +38,58 @@ struct CombineArgs {
 // SSP-RK3 stage combination (Eq. Runge-kutta); counts non-physical cells of
 // the stage input.
 template <int ND>
-__global__ void combine_kernel(CombineArgs a)
+__global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
 {
     constexpr int nc = ND + 2;
-    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < a.ncell;
-         id += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t x = id % a.n[0], y = (id / a.n[0]) % a.n[1], z = id / (a.n[0] * a.n[1]);
-        int64_t flo[3];
+    // one thread per cell; x from the block's row, y and z from the grid
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.n[0]) return;
+    const int64_t y = blockIdx.y, z = blockIdx.z;
+    const int64_t id = x + a.n[0] * (y + a.n[1] * z);
+    int64_t flo[3];
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        const int64_t fn0 = a.n[0] + (d == 0), fn1 = a.n[1] + (d == 1);
+        flo[d] = x + fn0 * (y + fn1 * z);
+    }
+    double Uc[nc];
+#pragma unroll
+    for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
+    {
+        // the non-physical test of cell_quantities: rho > 0, p > 0, c and H
+        // finite (c = sqrt(gamma p / rho) is finite exactly when its
+        // argument is, for p > 0)
+        const double rho = Uc[0], E = Uc[nc - 1];
+        const double rinv = 1.0 / rho;
+        double t = Uc[1] * (Uc[1] * rinv);
+#pragma unroll
+        for (int k = 1; k < ND; k++) t = fma(Uc[1 + k], Uc[1 + k] * rinv, t);
+        const double p = a.K.gm1 * (E - 0.5 * t);
+        const double c2 = (a.K.gamma * p) * rinv;
+        const double Hc = (E + p) * rinv;
+        if (!(rho > 0.0) || !(p > 0.0) || !isfinite(c2) || !isfinite(Hc))
+            atomicAdd(&a.st->nonphys, 1ull);
+    }
+    const double dt = a.st->dt;
+#pragma unroll
+    for (int c = 0; c < nc; c++) {
+        double acc = 0.0;
 #pragma unroll
         for (int d = 0; d < ND; d++) {
-            const int64_t fn0 = a.n[0] + (d == 0), fn1 = a.n[1] + (d == 1);
-            flo[d] = x + fn0 * (y + fn1 * z);
+            const double *Fd = a.F[d] + c * a.nfaces[d];
+            const double t = (Fd[flo[d] + a.fstride[d]] - Fd[flo[d]]) * a.inv_dx[d];
+            acc = acc - t;
         }
-        double Uc[nc];
-#pragma unroll
-        for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
-        {
-            CellQ<ND> q;
-            cell_quantities<ND, 0>(Uc, a.K, q);
-            if (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H))
-                atomicAdd(&a.st->nonphys, 1ull);
+        double o;
+        if (a.mode == 0) {
+            o = acc;
+        } else {
+            const double t = Uc[c] + dt * acc;
+            if (a.mode == 1) o = t;
+            else if (a.mode == 2) o = 0.75 * a.Un[c * a.ncell + id] + 0.25 * t;
+            else o = (1.0 / 3.0) * a.Un[c * a.ncell + id] + (2.0 / 3.0) * t;
         }
-        const double dt = a.st->dt;
-#pragma unroll
-        for (int c = 0; c < nc; c++) {
-            double acc = 0.0;
-#pragma unroll
-            for (int d = 0; d < ND; d++) {
-                const double *Fd = a.F[d] + c * a.nfaces[d];
-                const double t = (Fd[flo[d] + a.fstride[d]] - Fd[flo[d]]) * a.inv_dx[d];
-                acc = acc - t;
-            }
-            double o;
-            if (a.mode == 0) {
-                o = acc;
-            } else {
-                const double t = Uc[c] + dt * acc;
-                if (a.mode == 1) o = t;
-                else if (a.mode == 2) o = 0.75 * a.Un[c * a.ncell + id] + 0.25 * t;
-                else o = (1.0 / 3.0) * a.Un[c * a.ncell + id] + (2.0 / 3.0) * t;
-            }
-            a.out[c * a.ncell + id] = o;
-        }
+        a.out[c * a.ncell + id] = o;
     }
 }
 
@@ -247,7 +257,7 @@ static int validate(const teno_params *p)
             return TENO_EINVAL;
         }
     }
-    if (p->n[1] > 65535 || p->n[2] > 65535 * 8) return TENO_EINVAL;   // grid limits
+    if (p->n[1] > 65535 || p->n[2] > 65535) return TENO_EINVAL;   // grid y / z limits
     return TENO_OK;
 }
 
@@ -404,7 +414,8 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     c.ncell = ncells(p);
     c.mode = mode;
     c.K = K;
-    const int blk = 256, grd = grid_for(c.ncell, blk);
+    const int blk = 256;
+    const dim3 grd((unsigned)((p->n[0] + blk - 1) / blk), (unsigned)p->n[1], (unsigned)p->n[2]);
     if (nd == 1) combine_kernel<1><<<grd, blk, 0, s>>>(c);
     else if (nd == 2) combine_kernel<2><<<grd, blk, 0, s>>>(c);
     else combine_kernel<3><<<grd, blk, 0, s>>>(c);

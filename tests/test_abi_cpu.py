@@ -61,6 +61,7 @@ def test_workspace_sizing(lib):
     dict(scheme=9), dict(ndim=4), dict(q=2), dict(gamma=1.0), dict(n=[3]),
     dict(bc_lo=[0], bc_hi=[1]), dict(bc_lo=[5], bc_hi=[5]), dict(dx=[0.0]),
     dict(flux_split=2), dict(limiter=2), dict(ct_cr=0.0), dict(n=[64, 2]),
+    dict(ndim=3, n=[8, 8, 65536], dx=[0.1] * 3), dict(ndim=2, n=[8, 65536], dx=[0.1] * 2),
 ])
 def test_invalid_parameters(lib, bad):
     kw = dict(ndim=1, n=[64], dx=[0.1], scheme=8)

@@ -48,6 +48,13 @@ extern "C" {
 #define TENO_BC_TRANSMISSIVE 1 /* zero-order extrapolation: ghost = end cell  */
 #define TENO_BC_SLIPWALL 2     /* App. A.1: ghost -r = cell r-1, normal
                                   momentum negated                            */
+#define TENO_BC_NOSLIP 3       /* App. A.2: ghost -r = cell r-1, all momentum
+                                  components negated                          */
+#define TENO_BC_DIRICHLET 4    /* App. A.3: given boundary-face primitive
+                                  state phi' (bc_state_lo / bc_state_hi),
+                                  ghost -r primitives = 2 phi' - those of cell
+                                  r-1 (second order); not differentiated by
+                                  the adjoint calls, not in batched mode      */
 
 /* Flux splitting of the characteristic fluxes (Sec. 5). */
 #define TENO_SPLIT_LLF 0       /* per field k: alpha_k = max |lambda_k| over
@@ -75,6 +82,16 @@ typedef struct teno_params {
     int32_t bc_lo[3];      /* TENO_BC_* at the low end of each axis             */
     int32_t bc_hi[3];      /* TENO_BC_* at the high end of each axis            */
     int32_t reserved;      /* must be 0                                          */
+    /* TENO_BC_DIRICHLET boundary states, caller-owned device arrays (16-byte
+     * aligned), read on every right-hand-side evaluation (the caller may
+     * update them between calls, e.g. a time-dependent inflow); NULL for
+     * other sides.  Layout for axis d: primitives (rho, u_0 .. u_{ndim-1}, p)
+     * major, then the boundary faces in the order of the two other axes,
+     * x fastest: state[q * m + s], m = product of n over the axes != d,
+     * s = the face's index among them (d = 0: y + n[1] z; d = 1: x + n[0] z;
+     * d = 2: x + n[0] y). */
+    const double *bc_state_lo[3];
+    const double *bc_state_hi[3];
 } teno_params;
 
 /* Fill *p with the paper's built-in parameters (eps = 1e-40, q = 7 of Sec.
@@ -153,7 +170,7 @@ typedef struct teno_batch_problem {
     double dx;             /* spacing (> 0)                                     */
     int32_t scheme;        /* 8 or 10                                           */
     int32_t limiter;       /* 0 or 1 (positivity-preserving limiter, Sec. 5.3) */
-    int32_t bc_lo, bc_hi;  /* TENO_BC_* at the two ends                         */
+    int32_t bc_lo, bc_hi;  /* TENO_BC_* at the two ends, not TENO_BC_DIRICHLET  */
 } teno_batch_problem;
 
 typedef struct teno_batch teno_batch;   /* opaque host-side plan */

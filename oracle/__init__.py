@@ -26,7 +26,7 @@ _LIB = os.path.join(_BUILD, "libteno_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_SLIPWALL = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_SLIPWALL, BC_NOSLIP, BC_DIRICHLET = 0, 1, 2, 3, 4
 SPLIT_LLF, SPLIT_RUSANOV = 0, 1
 
 
@@ -53,15 +53,28 @@ class Params(ctypes.Structure):
         ("eps_beta", ctypes.c_double), ("eps_eta", ctypes.c_double),
         ("lim_eps", ctypes.c_double),
         ("bc_lo", ctypes.c_int32 * 3), ("bc_hi", ctypes.c_int32 * 3),
+        ("bc_state_lo", ctypes.c_void_p * 3), ("bc_state_hi", ctypes.c_void_p * 3),
     ]
 
 
 def params(ndim, n, dx, scheme=8, gamma=1.4, bc=BC_PERIODIC, bc_lo=None, bc_hi=None,
            split=SPLIT_LLF, limiter=0, alpha1=14.0, alpha2=6.4, cr=0.265,
-           eps_beta=1e-40, eps_eta=1e-40, lim_eps=1e-13) -> Params:
+           eps_beta=1e-40, eps_eta=1e-40, lim_eps=1e-13, bc_state_lo=None,
+           bc_state_hi=None) -> Params:
     """Parameter block with the paper's built-in values as defaults (Sec. 3.2,
-    Sec. 3.4: eps = 1e-40, q = 7, C_r = 0.265, alpha1 = 14, alpha2 = 6.4)."""
+    Sec. 3.4: eps = 1e-40, q = 7, C_r = 0.265, alpha1 = 14, alpha2 = 6.4).
+    bc_state_lo / bc_state_hi: per axis None or the BC_DIRICHLET boundary-face
+    primitives (rho, u..., p) as an array [ndim + 2][faces of the side, other
+    axes x fastest] (App. A.3); the block keeps them alive."""
     p = Params()
+    p._keep = []
+    for name, states in (("bc_state_lo", bc_state_lo), ("bc_state_hi", bc_state_hi)):
+        states = list(states or []) + [None] * 3
+        for a in range(3):
+            if states[a] is not None:
+                arr = np.ascontiguousarray(states[a], np.float64)
+                p._keep.append(arr)
+                getattr(p, name)[a] = arr.ctypes.data
     p.ndim, p.scheme, p.split, p.limiter = ndim, scheme, split, limiter
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))

@@ -34,7 +34,7 @@
 #define MAXC 5          /* conserved variables in 3D: rho, m_x, m_y, m_z, E */
 #define MAXH 5          /* half-width of the ten-point stencil                */
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_SLIPWALL = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_SLIPWALL = 2, BC_NOSLIP = 3, BC_DIRICHLET = 4 };
 enum { SPLIT_LLF = 0, SPLIT_RUSANOV = 1 };
 
 /* Oracle-private parameter block (its own layout; the CUDA library has another). */
@@ -44,6 +44,9 @@ typedef struct {
     double dx[3];
     double gamma, alpha1, alpha2, cr, eps_beta, eps_eta, lim_eps;
     int32_t bc_lo[3], bc_hi[3];
+    /* BC_DIRICHLET: boundary-face primitives (rho, u..., p) of each side,
+     * [ndim + 2][faces of the side, other axes x fastest]; NULL otherwise */
+    const double *bc_state_lo[3], *bc_state_hi[3];
 } or_params;
 
 /* ------------------------------------------------------------------------- */
@@ -387,23 +390,58 @@ typedef struct {
 } cellq;
 
 /* Map a (possibly ghost) index along one axis to an interior index (App. A).
- * *mirror = 1 when the slip-wall rule negates the wall-normal momentum. */
-static int64_t map_index(int64_t j, int64_t n, int bc_lo, int bc_hi, int *mirror)
+ * *side = -1 / +1 when the cell is a ghost of a wall or Dirichlet side (the
+ * rule then applies to the returned mirror cell), 0 otherwise. */
+static int64_t map_index(int64_t j, int64_t n, int bc_lo, int bc_hi, int *side)
 {
-    *mirror = 0;
+    *side = 0;
     if (j < 0) {
         if (bc_lo == BC_PERIODIC) return ((j % n) + n) % n;   /* ghost -r = n-r */
         if (bc_lo == BC_TRANSMISSIVE) return 0;              /* zero-order extrapolation */
-        *mirror = 1;
-        return -j - 1;                                       /* ghost -r = r-1 */
+        *side = -1;
+        return -j - 1;                                       /* ghost -r <- cell r-1 */
     }
     if (j >= n) {
         if (bc_hi == BC_PERIODIC) return j % n;              /* ghost n-1+r = r-1 */
         if (bc_hi == BC_TRANSMISSIVE) return n - 1;
-        *mirror = 1;
-        return 2 * n - 1 - j;                                /* ghost n-1+r = n-r */
+        *side = 1;
+        return 2 * n - 1 - j;                                /* ghost n-1+r <- cell n-r */
     }
     return j;
+}
+
+/* App. A.3, Dirichlet: the ghost's primitive variables are 2 phi' - phi,
+ * phi those of the mirror cell (in Uc on entry) and phi' the given state of
+ * the boundary face the ghost row belongs to (st, faces numbered over the
+ * other axes, x fastest); the ghost is returned as conserved variables. */
+static void dirichlet_ghost(const or_params *P, int d, const double *st, const int64_t x[3],
+                            double *Uc)
+{
+    int nd = P->ndim, nc = nd + 2;
+    int64_t m = 1, s = 0;
+    for (int a = 0; a < 3; a++) {
+        if (a == d) continue;
+        s += x[a] * m;
+        m *= P->n[a];
+    }
+    double gm1 = P->gamma - 1.0;
+    /* phi of the mirror cell */
+    double rho = Uc[0], E = Uc[nc - 1];
+    double rinv = 1.0 / rho, u[3];
+    for (int a = 0; a < nd; a++) u[a] = Uc[1 + a] * rinv;
+    double t = Uc[1] * u[0];
+    for (int a = 1; a < nd; a++) t = fma(Uc[1 + a], u[a], t);
+    double p = gm1 * (E - 0.5 * t);
+    /* reflected about phi' */
+    double rg = 2.0 * st[s] - rho, ug[3];
+    for (int a = 0; a < nd; a++) ug[a] = 2.0 * st[(1 + a) * m + s] - u[a];
+    double pg = 2.0 * st[(nc - 1) * m + s] - p;
+    /* back to conserved variables: E = p / (gamma - 1) + rho |u|^2 / 2 */
+    Uc[0] = rg;
+    for (int a = 0; a < nd; a++) Uc[1 + a] = rg * ug[a];
+    double k2 = Uc[1] * ug[0];
+    for (int a = 1; a < nd; a++) k2 = fma(Uc[1 + a], ug[a], k2);
+    Uc[nc - 1] = pg / gm1 + 0.5 * k2;
 }
 
 static int64_t lin_index(const or_params *P, const int64_t x[3])
@@ -419,12 +457,21 @@ static int64_t ncells(const or_params *P)
 static void load_cell(const or_params *P, const double *U, int d, const int64_t base[3],
                       int64_t j, double *out)
 {
-    int nc = P->ndim + 2, mir;
+    int nc = P->ndim + 2, side;
     int64_t x[3] = {base[0], base[1], base[2]};
-    x[d] = map_index(j, P->n[d], P->bc_lo[d], P->bc_hi[d], &mir);
+    x[d] = map_index(j, P->n[d], P->bc_lo[d], P->bc_hi[d], &side);
     int64_t id = lin_index(P, x), N = ncells(P);
     for (int c = 0; c < nc; c++) out[c] = U[c * N + id];
-    if (mir) out[1 + d] = -out[1 + d];
+    if (side) {
+        int bc = side < 0 ? P->bc_lo[d] : P->bc_hi[d];
+        if (bc == BC_SLIPWALL) {                  /* App. A.1: normal velocity negated */
+            out[1 + d] = -out[1 + d];
+        } else if (bc == BC_NOSLIP) {             /* App. A.2: all velocity negated */
+            for (int a = 0; a < P->ndim; a++) out[1 + a] = -out[1 + a];
+        } else {                                  /* App. A.3 */
+            dirichlet_ghost(P, d, side < 0 ? P->bc_state_lo[d] : P->bc_state_hi[d], x, out);
+        }
+    }
 }
 
 /* Primitive variables, sound speed, enthalpy and the physical flux along d. */

@@ -19,6 +19,7 @@ from . import _build
 
 TENO_OK, TENO_EINVAL, TENO_ECUDA, TENO_ENONPHYSICAL, TENO_ETIMEOUT = 0, 1, 2, 3, 4
 TENO_BC_PERIODIC, TENO_BC_TRANSMISSIVE, TENO_BC_SLIPWALL = 0, 1, 2
+TENO_BC_NOSLIP, TENO_BC_DIRICHLET = 3, 4
 TENO_SPLIT_LLF, TENO_SPLIT_RUSANOV = 0, 1
 
 _lock = threading.Lock()
@@ -53,6 +54,7 @@ class teno_params(ctypes.Structure):
         ("limiter_eps", ctypes.c_double), ("q", ctypes.c_int32),
         ("bc_lo", ctypes.c_int32 * 3), ("bc_hi", ctypes.c_int32 * 3),
         ("reserved", ctypes.c_int32),
+        ("bc_state_lo", ctypes.c_void_p * 3), ("bc_state_hi", ctypes.c_void_p * 3),
     ]
 
 
@@ -166,11 +168,22 @@ def teno_strerror(code: int) -> str:
 
 def teno_params_init(**kw) -> teno_params:
     """Paper defaults (Sec. 3.2, 3.4), then keyword overrides.  Sequences for
-    n, dx, bc_lo, bc_hi are padded to three axes (n: 1, dx: 1.0, bc: 0)."""
+    n, dx, bc_lo, bc_hi are padded to three axes (n: 1, dx: 1.0, bc: 0).
+    bc_state_lo / bc_state_hi: per axis a device tensor (or None) holding the
+    TENO_BC_DIRICHLET boundary-face primitives, [ndim + 2][faces of the side]
+    (include/teno.h); the caller keeps the tensors alive while p is used."""
     p = teno_params()
     load().teno_params_init(ctypes.byref(p))
     for k, v in kw.items():
-        if k in ("n", "dx", "bc_lo", "bc_hi"):
+        if k in ("bc_state_lo", "bc_state_hi"):
+            v = list(v) + [None] * (3 - len(v))
+            arr = getattr(p, k)
+            for i in range(3):
+                if v[i] is None or isinstance(v[i], int):
+                    arr[i] = v[i]
+                else:
+                    arr[i] = _ptr(v[i]).value
+        elif k in ("n", "dx", "bc_lo", "bc_hi"):
             v = list(v)
             pad = {"n": 1, "dx": 1.0, "bc_lo": 0, "bc_hi": 0}[k]
             v = v + [pad] * (3 - len(v))

@@ -249,11 +249,15 @@ static int validate(const teno_params *p)
             if (!(p->dx[a] > 0.0)) return TENO_EINVAL;
             for (int side = 0; side < 2; side++) {
                 const int b = side ? p->bc_hi[a] : p->bc_lo[a];
-                if (b < TENO_BC_PERIODIC || b > TENO_BC_SLIPWALL) return TENO_EINVAL;
+                const double *st = side ? p->bc_state_hi[a] : p->bc_state_lo[a];
+                if (b < TENO_BC_PERIODIC || b > TENO_BC_DIRICHLET) return TENO_EINVAL;
+                // a state array exactly on the Dirichlet sides (16-byte aligned)
+                if ((b == TENO_BC_DIRICHLET) != (st != nullptr)) return TENO_EINVAL;
+                if (st && ((uintptr_t)st & 15)) return TENO_EINVAL;
             }
             if ((p->bc_lo[a] == TENO_BC_PERIODIC) != (p->bc_hi[a] == TENO_BC_PERIODIC))
                 return TENO_EINVAL;
-        } else if (p->n[a] != 1) {
+        } else if (p->n[a] != 1 || p->bc_state_lo[a] || p->bc_state_hi[a]) {
             return TENO_EINVAL;
         }
     }
@@ -380,6 +384,8 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.nfaces = face_grid(p, d);
         a.bc_lo = p->bc_lo[d];
         a.bc_hi = p->bc_hi[d];
+        a.bcs_lo = p->bc_state_lo[d];
+        a.bcs_hi = p->bc_state_hi[d];
         a.lam = &st->lam[d];
         a.fast = g_fast_filter;
         a.exact_count = g_prof.on ? g_prof.exact : nullptr;

@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         const int j = idx / TP, p = idx % TP;
         const int64_t pg = ps + p;
         if (pg >= npen) continue;
-        bool mir;
-        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, mir);
+        int rule;                      // 0 copy, 1 slip-wall / 2 no-slip mirror
+        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, rule);
         int64_t id;
         if (D == 0) id = gi + n0 * (pg + n1 * z);
         else if (D == 1) id = pg + n0 * (gi + n1 * z);
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
-        if (mir) Uc[1 + D] = -Uc[1 + D];
+        apply_ghost_rule<ND, D>(Uc, rule, nullptr, nullptr, 0, 0, gm1);
         CellQ<ND> q;
         cell_quantities<ND, D>(Uc, a.K, q);
 #pragma unroll
@@ -566,19 +566,22 @@ __global__ void adj_gather_kernel(AdjArgs a, double *mu, int accumulate)
         double Ut[nc], Fs[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) { Ut[c] = 0.0; Fs[c] = 0.0; }
-        // candidate positions g along D that map to cell i, with mirror flag
+        // candidate positions g along D that map to cell i, with the mirror
+        // rule of their image (0 none, 1 slip wall, 2 no-slip)
         int64_t gs[2 * 5 + 3];
-        bool ms[2 * 5 + 3];
+        int ms[2 * 5 + 3];
         int ng = 0;
-        gs[ng] = i; ms[ng] = false; ng++;
-        if (a.bc_lo == 0) { gs[ng] = i - nD; ms[ng] = false; ng++; }
-        if (a.bc_hi == 0) { gs[ng] = i + nD; ms[ng] = false; ng++; }
+        gs[ng] = i; ms[ng] = 0; ng++;
+        if (a.bc_lo == 0) { gs[ng] = i - nD; ms[ng] = 0; ng++; }
+        if (a.bc_hi == 0) { gs[ng] = i + nD; ms[ng] = 0; ng++; }
         if (a.bc_lo == 1 && i == 0)
-            for (int r = 1; r <= H; r++) { gs[ng] = -r; ms[ng] = false; ng++; }
+            for (int r = 1; r <= H; r++) { gs[ng] = -r; ms[ng] = 0; ng++; }
         if (a.bc_hi == 1 && i == nD - 1)
-            for (int r = 0; r < H; r++) { gs[ng] = nD + r; ms[ng] = false; ng++; }
-        if (a.bc_lo == 2 && i < H) { gs[ng] = -i - 1; ms[ng] = true; ng++; }
-        if (a.bc_hi == 2 && i >= nD - H) { gs[ng] = 2 * nD - 1 - i; ms[ng] = true; ng++; }
+            for (int r = 0; r < H; r++) { gs[ng] = nD + r; ms[ng] = 0; ng++; }
+        if ((a.bc_lo == 2 || a.bc_lo == 3) && i < H) { gs[ng] = -i - 1; ms[ng] = a.bc_lo - 1; ng++; }
+        if ((a.bc_hi == 2 || a.bc_hi == 3) && i >= nD - H) {
+            gs[ng] = 2 * nD - 1 - i; ms[ng] = a.bc_hi - 1; ng++;
+        }
         for (int q = 0; q < ng; q++) {
             const int64_t g = gs[q];
             if (g < -H || g > nD + H - 1) continue;
@@ -601,12 +604,14 @@ __global__ void adj_gather_kernel(AdjArgs a, double *mu, int accumulate)
 #pragma unroll
                 for (int c = 0; c < nc; c++) { Ut[c] += Us[c]; Fs[c] += Fm[c]; }
             } else {
+                // the image is the mirror map M U (M diagonal, +-1): its flux
+                // Jacobian is taken at M U and M^T = M maps the adjoint back
                 double Ug[nc], Ub[nc];
 #pragma unroll
                 for (int c = 0; c < nc; c++) { Ug[c] = Uc[c]; Ub[c] = Us[c]; }
-                Ug[1 + D] = -Ug[1 + D];
+                apply_ghost_rule<ND, D>(Ug, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
                 flux_adjoint<ND, D>(Ug, Fm, a.K.gm1, Ub);
-                Ub[1 + D] = -Ub[1 + D];
+                apply_ghost_rule<ND, D>(Ub, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
 #pragma unroll
                 for (int c = 0; c < nc; c++) Ut[c] += Ub[c];
             }
@@ -743,6 +748,8 @@ int check_adj(const teno_params *p, void *ws, size_t ws_bytes)
     int r = teno_workspace_bytes(p, &b);
     if (r) return r;
     if (p->limiter) return TENO_EINVAL;
+    for (int d = 0; d < p->ndim; d++)
+        if (p->bc_lo[d] == TENO_BC_DIRICHLET || p->bc_hi[d] == TENO_BC_DIRICHLET) return TENO_EINVAL;
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < adj_layout(p).total) return TENO_EINVAL;
     return TENO_OK;
 }

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(TF) batch_face_kernel(
         a.nfaces = d.n + 1;
         a.bc_lo = d.bc_lo;
         a.bc_hi = d.bc_hi;
+        a.bcs_lo = nullptr;
+        a.bcs_hi = nullptr;
         a.lam = &slots[p].lam;
         a.fast = fast;
         a.exact_count = nullptr;
@@ -216,6 +218,7 @@ int problem_params(const teno_batch *b, int p, teno_params *pp)
     pp->limiter = q.limiter;
     pp->bc_lo[0] = q.bc_lo; pp->bc_hi[0] = q.bc_hi;
     pp->bc_lo[1] = pp->bc_lo[2] = pp->bc_hi[1] = pp->bc_hi[2] = 0;
+    for (int a = 0; a < 3; a++) pp->bc_state_lo[a] = pp->bc_state_hi[a] = nullptr;   // no Dirichlet
     size_t bytes;
     return teno_workspace_bytes(pp, &bytes);
 }

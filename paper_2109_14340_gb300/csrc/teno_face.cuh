@@ -26,6 +26,7 @@ struct FaceArgs {
     int64_t n[3];
     int64_t ncell, nfaces;
     int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
+    const double *bcs_lo, *bcs_hi;   // Dirichlet boundary-face states of axis D, or nullptr
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
     unsigned long long *exact_count;   // adds the exact-path reconstructions, or nullptr
@@ -33,22 +34,74 @@ struct FaceArgs {
     Consts K;
 };
 
-// App. A ghost-cell rules along one axis; mir = slip-wall mirror.  The final
-// clamp only matters for padding cells beyond the last face of a tile.
-__device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int lo, int hi, bool &mir)
+// App. A ghost-cell rules along one axis.  Returns the interior cell whose
+// state defines the (possibly ghost) cell j, and the rule to apply to it:
+// 0 copy, 1 slip-wall mirror (wall-normal momentum negated), 2 no-slip
+// mirror (all momentum negated), 3 / 4 Dirichlet reflection about the low /
+// high boundary-face state.  The final clamp only matters for padding cells
+// beyond the last face of a tile.
+__device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int lo, int hi, int &rule)
 {
-    mir = false;
+    rule = 0;
     int64_t r = j;
     if (j < 0) {
         if (lo == 0) r = ((j % n) + n) % n;
         else if (lo == 1) r = 0;
-        else { mir = true; r = -j - 1; }
+        else { rule = lo == 2 ? 1 : (lo == 3 ? 2 : 3); r = -j - 1; }
     } else if (j >= n) {
         if (hi == 0) r = j % n;
         else if (hi == 1) r = n - 1;
-        else { mir = true; r = 2 * n - 1 - j; }
+        else { rule = hi == 2 ? 1 : (hi == 3 ? 2 : 4); r = 2 * n - 1 - j; }
     }
     return r < 0 ? 0 : (r >= n ? n - 1 : r);
+}
+
+// Ghost state of a Dirichlet side (App. A.3): the mirror cell's primitives
+// phi (with the exact path's arithmetic for p) reflected about the boundary
+// face's primitives phi' as 2 phi' - phi, then back to conserved variables.
+// st: the side's state array, m faces per primitive, s this face.
+template <int ND>
+__device__ __forceinline__ void dirichlet_ghost(double (&Uc)[ND + 2], const double *st, int64_t m,
+                                                int64_t s, double gm1)
+{
+    constexpr int nc = ND + 2;
+    const double rho = Uc[0], E = Uc[nc - 1];
+    const double rinv = 1.0 / rho;
+    double u[ND];
+#pragma unroll
+    for (int a = 0; a < ND; a++) u[a] = Uc[1 + a] * rinv;
+    double t = Uc[1] * u[0];
+#pragma unroll
+    for (int a = 1; a < ND; a++) t = fma(Uc[1 + a], u[a], t);
+    const double p = gm1 * (E - 0.5 * t);
+    const double rg = 2.0 * st[s] - rho;
+    double ug[ND];
+#pragma unroll
+    for (int a = 0; a < ND; a++) ug[a] = 2.0 * st[(1 + a) * m + s] - u[a];
+    const double pg = 2.0 * st[(nc - 1) * m + s] - p;
+    Uc[0] = rg;
+#pragma unroll
+    for (int a = 0; a < ND; a++) Uc[1 + a] = rg * ug[a];
+    double k2 = Uc[1] * ug[0];
+#pragma unroll
+    for (int a = 1; a < ND; a++) k2 = fma(Uc[1 + a], ug[a], k2);
+    Uc[nc - 1] = pg / gm1 + 0.5 * k2;
+}
+
+// Applies a ghost rule of map_index to the loaded state of the mirror cell.
+template <int ND, int D>
+__device__ __forceinline__ void apply_ghost_rule(double (&Uc)[ND + 2], int rule, const double *st_lo,
+                                                 const double *st_hi, int64_t m, int64_t s,
+                                                 double gm1)
+{
+    if (rule == 1) {
+        Uc[1 + D] = -Uc[1 + D];
+    } else if (rule == 2) {
+#pragma unroll
+        for (int a = 0; a < ND; a++) Uc[1 + a] = -Uc[1 + a];
+    } else if (rule >= 3) {
+        dirichlet_ghost<ND>(Uc, rule == 3 ? st_lo : st_hi, m, s, gm1);
+    }
 }
 
 template <int ND>
@@ -119,8 +172,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         const int j = idx / TP, p = idx % TP;
         const int64_t pg = pstart + p;
         if (pg >= npen) continue;
-        bool mir;
-        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, mir);
+        int rule;
+        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, rule);
         int64_t id;
         if (D == 0) id = gi + n0 * (pg + n1 * z);
         else if (D == 1) id = pg + n0 * (gi + n1 * z);
@@ -128,7 +181,12 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
-        if (mir) Uc[1 + D] = -Uc[1 + D];
+        if (rule) {
+            // boundary-face index among the faces of this side (other axes, x fastest)
+            const int64_t m = a.ncell / nD;
+            const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
+            apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
+        }
         CellQ<ND> q;
         cell_quantities<ND, D>(Uc, a.K, q);
 #pragma unroll

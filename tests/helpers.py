@@ -6,7 +6,8 @@ def oracle_params(case, **over):
     import oracle
     kw = dict(ndim=case["ndim"], n=case["n"], dx=case["dx"], scheme=case["scheme"],
               gamma=case["gamma"], bc_lo=case["bc_lo"], bc_hi=case["bc_hi"],
-              limiter=case.get("limiter", 0))
+              limiter=case.get("limiter", 0), bc_state_lo=case.get("bc_state_lo"),
+              bc_state_hi=case.get("bc_state_hi"))
     kw.update(over)
     return oracle.params(**kw)
 

@@ -54,7 +54,21 @@ CASES = [
     ("2d-mixed-s8-llf", 2, [24, 20], 8, [1, 0], [1, 0], 0),
     ("2d-slip-s10-llf", 2, [20, 22], 10, [2, 1], [2, 1], 0),
     ("3d-periodic-s10-llf", 3, [12, 11, 10], 10, [0, 0, 0], [0, 0, 0], 0),
+    ("2d-noslip-s8-llf", 2, [22, 20], 8, [3, 0], [2, 0], 0),
+    ("3d-noslip-s10-rus", 3, [12, 11, 10], 10, [3, 1, 0], [1, 3, 0], 1),
 ]
+
+
+def test_adjoint_rejects_dirichlet():
+    """The adjoint calls do not differentiate Dirichlet ghosts (App. A.3)."""
+    st = torch.ones(4, 20, dtype=torch.float64, device=DEV)
+    p = T.teno_params_init(ndim=2, n=[20, 18], dx=[0.05, 0.05], scheme=8, bc_lo=[0, 4],
+                           bc_hi=[0, 1], bc_state_lo=[None, st])
+    aws = T.aligned_workspace(T.teno_adjoint_workspace_bytes(p), DEV)
+    U = torch.ones(4, 360, dtype=torch.float64, device=DEV)
+    with pytest.raises(T.TenoError) as e:
+        T.teno_rhs_vjp(p, U, U.clone(), torch.empty_like(U), None, aws)
+    assert e.value.code == T.TENO_EINVAL
 
 
 @pytest.mark.parametrize("name,nd,n,scheme,lo,hi,split", CASES, ids=[c[0] for c in CASES])

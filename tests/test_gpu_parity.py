@@ -30,8 +30,17 @@ def gpu_params(case, **over):
     kw = dict(ndim=case["ndim"], n=case["n"], dx=case["dx"], scheme=case["scheme"],
               gamma=case["gamma"], bc_lo=case["bc_lo"], bc_hi=case["bc_hi"],
               limiter=case.get("limiter", 0))
+    keep = []
+    for side in ("bc_state_lo", "bc_state_hi"):
+        st = case.get(side)
+        if st is not None:
+            t = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in st]
+            keep += t
+            kw[side] = t
     kw.update(over)
-    return T.teno_params_init(**kw)
+    p = T.teno_params_init(**kw)
+    p._keep = keep                        # the device states live as long as p
+    return p
 
 
 def both_params(case, split=0, limiter=None):
@@ -80,6 +89,15 @@ def _cases():
     out.append(("3d-random-walls", dict(U=U, ndim=3, n=n, dx=[0.1, 0.07, 0.05],
                                         bc_lo=[1, 2, 0], bc_hi=[2, 1, 0], scheme=10,
                                         gamma=1.4)))
+    # no-slip (App. A.2) and Dirichlet (App. A.3) sides
+    for scheme in (8, 10):
+        out.append(("1d-dirichlet-noslip-s%d" % scheme,
+                    workloads.boundary_walls(1, [97], [4], [3], seed=6001, scheme=scheme)))
+        out.append(("2d-dirichlet-noslip-s%d" % scheme,
+                    workloads.boundary_walls(2, [33, 27], [1, 4], [3, 4], seed=6002, scheme=scheme)))
+        out.append(("3d-dirichlet-noslip-s%d" % scheme,
+                    workloads.boundary_walls(3, [14, 11, 9], [4, 3, 0], [2, 4, 0], seed=6003,
+                                             scheme=scheme)))
     return out
 
 

@@ -374,3 +374,82 @@ def test_dimension_by_dimension():
     # sums over velocity components run in axis order, so swapping the axes
     # changes rounding only
     assert np.abs(r2 - r3).max() <= 1e-12 * np.abs(r2).max()
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+def test_noslip_equals_mirrored_periodic(scheme):
+    """No-slip walls in y (App. A.2: ghost -r = cell r-1 with every velocity
+    component negated) give exactly the RHS of the y-periodic problem on the
+    doubled domain whose upper half is the mirror image with both velocities
+    negated, restricted to the original half (x periodic throughout)."""
+    g = np.random.Generator(np.random.PCG64(21))
+    nx, ny = 12, 14
+    rho = g.uniform(0.5, 1.5, (ny, nx))
+    u = g.uniform(-0.5, 0.5, (ny, nx))
+    v = g.uniform(-0.5, 0.5, (ny, nx))
+    pr = g.uniform(0.5, 1.5, (ny, nx))
+    U = workloads.prim_to_cons(rho, [u, v], pr, 1.4)
+    U2 = workloads.prim_to_cons(np.concatenate([rho, rho[::-1]]),
+                                [np.concatenate([u, -u[::-1]]), np.concatenate([v, -v[::-1]])],
+                                np.concatenate([pr, pr[::-1]]), 1.4)
+    p1 = oracle.params(2, [nx, ny], [0.1, 0.1], scheme=scheme, bc_lo=[0, 3], bc_hi=[0, 3])
+    p2 = oracle.params(2, [nx, 2 * ny], [0.1, 0.1], scheme=scheme, bc=0)
+    r, _, _, _ = oracle.rhs(p1, U)
+    r2, _, _, _ = oracle.rhs(p2, U2)
+    assert np.array_equal(r, r2[:, :nx * ny])
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+def test_dirichlet_equals_padded_domain(scheme):
+    """Dirichlet sides in y (App. A.3: the ghost's primitives are 2 phi' - phi
+    of the mirror cell r-1) give exactly the RHS of a domain padded with those
+    ghost rows written out.  Dyadic primitives with gamma = 3 make every
+    conversion and the reflection exact, so the padded rows are the rule's
+    exact values; phi' varies along the boundary."""
+    g = np.random.Generator(np.random.PCG64(23))
+    H = scheme // 2
+    nx, ny = 10, 12
+    gam = 3.0
+    rho = 2.0 ** g.integers(0, 3, (ny, nx))                     # 1, 2, 4
+    u = g.integers(-8, 9, (ny, nx)) / 8.0
+    v = g.integers(-8, 9, (ny, nx)) / 8.0
+    pr = 1.0 + g.integers(0, 5, (ny, nx)) / 4.0
+    lo = np.stack([4.0 + g.integers(0, 3, nx) / 2.0, g.integers(-4, 5, nx) / 8.0,
+                   g.integers(-4, 5, nx) / 8.0, 2.0 + g.integers(0, 3, nx) / 4.0])
+    hi = np.stack([4.0 + g.integers(0, 3, nx) / 2.0, g.integers(-4, 5, nx) / 8.0,
+                   g.integers(-4, 5, nx) / 8.0, 2.0 + g.integers(0, 3, nx) / 4.0])
+    U = workloads.prim_to_cons(rho, [u, v], pr, gam)
+    # ghost rows -H..-1 from rows H-1..0, rows ny..ny+H-1 from rows ny-1..ny-H
+    prim = [rho, u, v, pr]
+    low = [2.0 * lo[q][None, :] - prim[q][H - 1::-1] for q in range(4)]
+    high = [2.0 * hi[q][None, :] - prim[q][:ny - H - 1:-1] for q in range(4)]
+    padded = [np.concatenate([low[q], prim[q], high[q]]) for q in range(4)]
+    Up = workloads.prim_to_cons(padded[0], [padded[1], padded[2]], padded[3], gam)
+    p1 = oracle.params(2, [nx, ny], [0.1, 0.1], scheme=scheme, gamma=gam, bc_lo=[0, 4],
+                       bc_hi=[0, 4], bc_state_lo=[None, lo], bc_state_hi=[None, hi])
+    p2 = oracle.params(2, [nx, ny + 2 * H], [0.1, 0.1], scheme=scheme, gamma=gam,
+                       bc_lo=[0, 1], bc_hi=[0, 1])
+    r, _, _, nb = oracle.rhs(p1, U)
+    r2, _, _, _ = oracle.rhs(p2, Up)
+    assert nb == 0
+    assert np.array_equal(r, r2[:, H * nx:(H + ny) * nx])
+
+
+def test_dirichlet_free_stream():
+    """A uniform flow whose Dirichlet boundary state is the flow itself stays
+    uniform up to the rounding of the primitive / conserved conversions."""
+    n = [9, 8, 7]
+    cells = int(np.prod(n))
+    state = (0.9, [0.3, -0.2, 0.1], 1.1)
+    U = workloads.prim_to_cons(np.full(cells, state[0]), [np.full(cells, a) for a in state[1]],
+                               np.full(cells, state[2]), 1.4)
+    sides = []
+    for d in range(3):
+        m = cells // n[d]
+        sides.append(np.stack([np.full(m, state[0])] + [np.full(m, a) for a in state[1]] +
+                              [np.full(m, state[2])]))
+    p = oracle.params(3, n, [0.1, 0.1, 0.1], scheme=10, bc=4, bc_state_lo=sides,
+                      bc_state_hi=sides)
+    r, _, _, nb = oracle.rhs(p, U)
+    assert nb == 0
+    assert np.abs(r).max() <= 1e-13 * np.abs(U).max() / 0.1

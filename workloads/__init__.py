@@ -14,6 +14,7 @@ Workloads, shaped like the paper's 1D/2D/3D shock and turbulence problems
   * tgv_3d            Mach-0.5 Taylor-Green field + k^-5/3 solenoidal noise
   * batched_1d        thousands of independent Riemann problems, uneven sizes
   * sod_1d, double_rarefaction_1d   textbook problems of Sec. 5.2 / 5.3
+  * boundary_walls    random flow with no-slip / Dirichlet sides (App. A.2, A.3)
 """
 from __future__ import annotations
 
@@ -258,3 +259,78 @@ def adjoint_2d(n: int = 512, ny: int | None = None, seed: int = 5001, scheme: in
     return _case(U, 2, [n, ny], [1.0 / n, 1.0 / ny], [TRANSMISSIVE, PERIODIC],
                  [TRANSMISSIVE, PERIODIC], scheme, gamma, U_target_ic=Ut, steps=200,
                  checkpoint_every=20)
+
+
+def boundary_walls(ndim: int, n, bc_lo, bc_hi, seed: int = 6001, scheme: int = 10,
+                   gamma: float = 1.4):
+    """Random smooth-plus-noise flow with no-slip and Dirichlet sides (App.
+    A.2, A.3).  The Dirichlet sides get seeded boundary-face primitives
+    (rho, u..., p) as arrays [ndim + 2][faces of the side, other axes x
+    fastest] under "bc_state_lo" / "bc_state_hi" (None for other sides)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    n = list(n) + [1] * (3 - len(n))
+    cells = n[0] * n[1] * n[2]
+    rho = g.uniform(0.4, 1.4, cells)
+    vel = [g.uniform(-0.6, 0.6, cells) for _ in range(ndim)]
+    pr = g.uniform(0.3, 1.5, cells)
+    U = prim_to_cons(rho, vel, pr, gamma)
+    lo = list(bc_lo) + [0] * (3 - len(bc_lo))
+    hi = list(bc_hi) + [0] * (3 - len(bc_hi))
+    st_lo, st_hi = [None] * 3, [None] * 3
+    for d in range(ndim):
+        m = cells // n[d]
+        for side, bcs, st in ((0, lo, st_lo), (1, hi, st_hi)):
+            if bcs[d] == 4:
+                # 2 phi' - phi stays positive: rho' >= 0.8 > 1.4 / 2, p' >= 0.9 > 1.5 / 2
+                st[d] = np.stack([g.uniform(0.8, 1.2, m)] +
+                                 [g.uniform(-0.4, 0.4, m) for _ in range(ndim)] +
+                                 [g.uniform(0.9, 1.3, m)])
+    dx = [0.1, 0.08, 0.06][:ndim]
+    return _case(U, ndim, n[:ndim], dx, lo[:ndim], hi[:ndim], scheme, gamma,
+                 bc_state_lo=st_lo, bc_state_hi=st_hi)
+
+
+def noh_3d(n: int = 64, scheme: int = 10, L: float = 0.256, gamma: float = 5.0 / 3.0,
+           p0: float = 1e-6):
+    """3D Noh implosion (Sec. 5.5): cube [0, L]^3, rho = 1, velocity -x_i / r
+    toward the origin, p = p0; symmetry (slip) walls at x_i = 0 and
+    supersonic inflow through the far faces, given there as Dirichlet states
+    (noh_inflow_states) with the initial velocity and pressure and the
+    analytic density.  Rusanov splitting, limiter on, t_end = 0.6."""
+    dx = L / n
+    c = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    U = prim_to_cons(np.ones_like(r).ravel(), [(-X / r).ravel(), (-Y / r).ravel(), (-Z / r).ravel()],
+                     np.full(r.size, p0), gamma)
+    return _case(U, 3, [n, n, n], [dx, dx, dx], [SLIPWALL] * 3, [4] * 3, scheme, gamma,
+                 L=L, p0=p0, t_end=0.6, split=1, limiter=1)
+
+
+def noh_density(r, t):
+    """Analytic density of the 3D Noh problem (Eq. density_noh): 64 behind the
+    shock r < t/3, (1 + t/r)^2 ahead of it."""
+    r = np.asarray(r, np.float64)
+    return np.where(r < t / 3.0, 64.0, (1.0 + t / np.maximum(r, 1e-300)) ** 2)
+
+
+def noh_inflow_states(case, t: float):
+    """Boundary-face primitives (rho, u, v, w, p) of the far faces x_d = L at
+    time t, [5][n*n] per axis, the other two axes x fastest: the analytic
+    density and the initial velocity -x_i / r and pressure."""
+    n, L, p0 = case["n"][0], case["L"], case["p0"]
+    dx = L / n
+    c = (np.arange(n) + 0.5) * dx
+    out = []
+    for d in range(3):
+        B, A = np.meshgrid(c, c, indexing="ij")       # (slow, fast) of the other two axes
+        coords = [None] * 3
+        others = [a for a in range(3) if a != d]
+        coords[d] = np.full_like(A, L)
+        coords[others[0]] = A
+        coords[others[1]] = B
+        r = np.sqrt(coords[0] ** 2 + coords[1] ** 2 + coords[2] ** 2)
+        st = np.stack([noh_density(r, t), -coords[0] / r, -coords[1] / r, -coords[2] / r,
+                       np.full_like(r, p0)])
+        out.append(st.reshape(5, -1))
+    return out

@@ -43,11 +43,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", type=int, default=10, choices=[8, 10])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", "--size", dest="n", type=int, default=256,
+                    help="cells per axis of the 3D workload (--size under torchrun, whose "
+                         "own options shadow --n)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-noh", action="store_true")
     ap.add_argument("--adjoint-n", type=int, default=512)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -225,6 +228,23 @@ def host_cores():
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ---------------------------------------------------------------------------
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, cells_per_rank: int, steps: int, seconds: float) -> float:
+    """Cell-updates per second of the whole job: every rank advances its own
+    problem of cells_per_rank cells by steps steps (weak scaling)."""
+    return world * cells_per_rank * steps / seconds
+
 
 def run_reference(args, rank):
     if rank != 0:
@@ -411,6 +431,63 @@ def run_adjoint(args, dev, stream):
             "loss": float(loss)}
 
 
+def run_noh(args, dev, stream, n=64, scheme=10, t_end=0.6):
+    """3D Noh implosion (Sec. 5.5) at 64^3 to t = 0.6: symmetry walls, inflow
+    faces as Dirichlet states with the analytic density, updated every step
+    from the host; Rusanov, limiter on.  Reports the rate of the whole loop
+    (CFL reduction read back for the host-side time, boundary states copied
+    in, RK3 step) and the solution against Eq. density_noh."""
+    import numpy as np
+    import torch
+
+    import paper_2109_14340_gb300 as T
+    import workloads
+    c = workloads.noh_3d(n, scheme=scheme)
+    st = [torch.from_numpy(a).to(dev) for a in workloads.noh_inflow_states(c, 0.0)]
+    p = T.teno_params_init(ndim=3, n=c["n"], dx=c["dx"], scheme=scheme, gamma=c["gamma"],
+                           bc_lo=c["bc_lo"], bc_hi=c["bc_hi"], flux_split=c["split"],
+                           limiter=c["limiter"], bc_state_hi=st)
+    S = T.Solver(p, dev)
+    U = torch.from_numpy(c["U"]).to(dev)
+    torch.cuda.synchronize(dev)
+    t, steps = 0.0, 0
+    t0 = time.perf_counter()
+    while t < t_end - 1e-12:
+        for d, a in enumerate(workloads.noh_inflow_states(c, t)):
+            st[d].copy_(torch.from_numpy(a))
+        dt = min(float(S.cfl_dt(U, 0.4).item()), t_end - t)
+        S.step(U, dt=dt)
+        t += dt
+        steps += 1
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    nonphys = S.status()
+    L = c["L"]
+    dx = L / n
+    cc = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(cc, cc, cc, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z).ravel()
+    rho = U[0].cpu().numpy()
+    R = t / 3.0
+    shell = np.floor(r / dx).astype(int)
+    k = np.arange(int(L / dx))
+    prof = np.array([rho[shell == i].mean() for i in k])
+    rc = np.array([r[shell == i].mean() for i in k])
+    ex = workloads.noh_density(rc, t)
+    r40 = float(rc[int(np.argmax((prof < 40.0) & (rc > 0.5 * R)))])
+    pre = rc > R + 6 * dx
+    post = (rc > 0.4 * R) & (rc < R - 4 * dx)
+    cell_pre = r > R + 6 * dx
+    exc = workloads.noh_density(r[cell_pre], t)
+    return {"workload": "3D Noh implosion %d^3 on [0,0.256]^3, gamma 5/3, TENO%d-AA, Rusanov, "
+                        "limiter, symmetry walls + Dirichlet inflow, to t = %.1f" % (n, scheme, t_end),
+            "steps": steps, "seconds": el, "value": n ** 3 * steps / el, "unit": "cell-updates/s",
+            "nonphysical": nonphys, "shock_radius": r40, "shock_radius_exact": R,
+            "pre_shock_shell_err_max": float((np.abs(prof[pre] - ex[pre]) / ex[pre]).max()),
+            "post_shock_mean_density": float(prof[post].mean()), "post_shock_exact": 64.0,
+            "pre_shock_cell_scatter_p99": float(np.percentile(np.abs(rho[cell_pre] - exc) / exc, 99))}
+
+
 def read_traffic_per_face(scheme):
     """Measured DRAM bytes per face of the face sweep, from the committed ncu
     summary (a line 'traffic_bytes_per_face[TENO<s>]: <value>')."""
@@ -484,12 +561,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     nonphys = solver.status()
 
-    t_max = ms
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * cells * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(world, cells, args.steps, t_max * 1e-3)
 
     # context: the same step with every decision evaluated in FP64 (filter
     # off), and one step from the same state both ways compared bitwise
@@ -529,12 +602,8 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         T.teno_advance_host(p, Uh, Ud2, 1, 0.4, ws2)
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = world * cells * k_e2e / t_e2e
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = whole_job_rate(world, cells, k_e2e, t_e2e)
     state_bytes = 5 * cells * 8
 
     # FP64 probe (context): measured DFMA rate on this GPU
@@ -572,6 +641,9 @@ def run_ours(args, rank, world, local_rank):
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(args, dev, stream)
+    noh = None
+    if not args.no_noh:
+        noh = run_noh(args, dev, stream)
 
     if rank != 0:
         if dist is not None:
@@ -628,6 +700,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "batched": batched,
         "adjoint": adjoint,
+        "noh": noh,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -23,6 +23,8 @@ struct CombineArgs {
     const double *F[3];      // face fluxes per direction, [nc][nfaces_d]
     int64_t nfaces[3];
     int64_t fstride[3];      // face-grid stride of the sweep axis in grid d
+    int wrap[3];             // periodic axis: the last cell's right face is face 0
+                             // (the same flux as face n, which may be left out)
     double inv_dx[3];
     const double *Uk;        // stage input (whose RHS the fluxes are)
     const double *Un;        // state at t^n (RK modes)
@@ -77,7 +79,10 @@ __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
 #pragma unroll
         for (int d = 0; d < ND; d++) {
             const double *Fd = a.F[d] + c * a.nfaces[d];
-            const double t = (Fd[flo[d] + a.fstride[d]] - Fd[flo[d]]) * a.inv_dx[d];
+            const int64_t xd = (d == 0) ? x : (d == 1 ? y : z);
+            const int64_t fr = (a.wrap[d] && xd == a.n[d] - 1) ? flo[d] - xd * a.fstride[d]
+                                                                : flo[d] + a.fstride[d];
+            const double t = (Fd[fr] - Fd[flo[d]]) * a.inv_dx[d];
             acc = acc - t;
         }
         double o;
@@ -388,12 +393,13 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.bcs_hi = p->bc_state_hi[d];
         a.lam = &st->lam[d];
         a.fast = g_fast_filter;
+        a.skip_last = (p->bc_lo[d] == TENO_BC_PERIODIC && !fl && !fz) ? 1 : 0;
         a.exact_count = g_prof.on ? g_prof.exact : nullptr;
         a.FK = fastk_of(p);
         a.K = K;
         const int slot = (g_prof.on && g_prof.used < ProfileRecord::kMax) ? g_prof.used++ : -1;
         if (slot >= 0) {
-            g_prof.nf[slot] = a.nfaces;
+            g_prof.nf[slot] = a.nfaces - (a.skip_last ? a.ncell / p->n[d] : 0);   // faces computed
             CUDA_TRY(profile_mark(0, slot, s));
         }
         cudaError_t e = (p->scheme == 8) ? launch_face8(nd, d, a, s) : launch_face10(nd, d, a, s);
@@ -410,6 +416,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         c.nfaces[d] = d < nd ? face_grid(p, d) : 0;
         const int64_t fn0 = p->n[0] + (d == 0), fn1 = p->n[1] + (d == 1);
         c.fstride[d] = d == 0 ? 1 : (d == 1 ? fn0 : fn0 * fn1);
+        c.wrap[d] = d < nd && p->bc_lo[d] == TENO_BC_PERIODIC;
     }
     c.inv_dx[0] = idx.x; c.inv_dx[1] = idx.y; c.inv_dx[2] = idx.z;
     c.Uk = Uk;

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(TF) batch_face_kernel(
         a.bcs_hi = nullptr;
         a.lam = &slots[p].lam;
         a.fast = fast;
+        a.skip_last = 0;
         a.exact_count = nullptr;
         a.FK = FK;
         a.K = K;

@@ -29,6 +29,8 @@ struct FaceArgs {
     const double *bcs_lo, *bcs_hi;   // Dirichlet boundary-face states of axis D, or nullptr
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
+    int skip_last;         // 1: face n of each line is not computed (periodic axis, no
+                           // decision record: its flux is face 0's, bitwise)
     unsigned long long *exact_count;   // adds the exact-path reconstructions, or nullptr
     FastK FK;
     Consts K;
@@ -116,10 +118,12 @@ struct SmemLayout {
 // Tile of the sweeps: TP pencils x TF faces along the sweep, the exact-path
 // queue's capacity in reconstructions per thread (QCAP) and the blocks per SM
 // the register allocation is bounded for (MINB).  A single line (1D) uses
-// 1 x 128.  Measured on GB300 (one 128-thread block = 8 x 16 faces):
-//   3D 256^3: three blocks per SM (168 registers, 64 KB shared memory each)
-//   beat two (at 8 x 16 or 16 x 8) by 8-9 % for TENO10 and TENO8, and
-//   4 x 16 / 8 x 8 at six; 2D 512^2 TENO8: all within 4 %, two blocks.
+// 1 x 128.  Measured on GB300 with 128-thread blocks:
+//   3D 256^3: three blocks per SM (168 registers, about 60 KB of shared
+//   memory each) beat two by 8-9 % and four by 9 %; with face n of periodic
+//   lines left out (256 faces per line), 4 x 32 beats 8 x 16 and 16 x 8 by
+//   0.5 % and 3 % (TENO10) and stages fewer halo cells per face;
+//   2D 512^2 TENO8: 4 x 32 ahead of 8 x 16 by 4 %.
 // TENO_FACE_TP/TF/QCAP/MINB, when defined, override every case (tuning).
 template <int ND, int H>
 struct FaceTile {
@@ -129,8 +133,8 @@ struct FaceTile {
     static constexpr int QCAP = TENO_FACE_QCAP;
     static constexpr int MINB = TENO_FACE_MINB;
 #else
-    static constexpr int TP = ND == 1 ? 1 : 8;
-    static constexpr int TF = ND == 1 ? 128 : 16;
+    static constexpr int TP = ND == 1 ? 1 : 4;
+    static constexpr int TF = ND == 1 ? 128 : 32;
     static constexpr int QCAP = 2;
     static constexpr int MINB = ND == 3 ? 3 : 1;
 #endif
@@ -206,7 +210,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 
     const int p = threadIdx.x % TP, fo = threadIdx.x / TP;
     const int64_t f = f0 + fo;
-    const bool active = !(f > nD || pstart + p >= npen);
+    const bool active = !(f > nD - a.skip_last || pstart + p >= npen);
     const int jl = fo + H - 1, jr = fo + H;           // cells i and i+1
 
     // Queue of reconstructions whose value is not computed in line (values,
@@ -492,10 +496,11 @@ cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
         attr_done = true;
     }
     dim3 grid;
-    if (D == 0) grid = dim3((unsigned)((a.n[0] + 1 + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
-    else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((a.n[1] + 1 + TF - 1) / TF), (unsigned)a.n[2]);
+    const int64_t nf = a.n[D] + 1 - a.skip_last;    // faces computed along D
+    if (D == 0) grid = dim3((unsigned)((nf + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
+    else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((nf + TF - 1) / TF), (unsigned)a.n[2]);
     else   // z tiles fastest: consecutive blocks share their halo planes through L2
-        grid = dim3((unsigned)((a.n[2] + 1 + TF - 1) / TF), (unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1]);
+        grid = dim3((unsigned)((nf + TF - 1) / TF), (unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1]);
     face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -28,7 +28,8 @@ struct AdjArgs {
     const double *U;        // state [nc][ncell]
     const double *lam;      // adjoint of L(U) [nc][ncell]
     const uint8_t *flags;   // decision record of this direction
-    double *slots;          // [nfaces][W][2 nc]: adjoint of U (direct) then of F
+    double *slots;          // [W][2 nc][nfaces]: per stencil position, the adjoint of U
+                            // (direct) then of F, faces contiguous
     int64_t n[3];
     int64_t ncell, nfaces;
     int bc_lo, bc_hi;
@@ -267,8 +268,12 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
     for (int k = 0; k < ND; k++) utb[k] = 0.0;
     double alphab[nc];
 
+    // A shear field's row of L is (-u_t, e_t, 0): only its columns 0 and
+    // 1 + t enter the sums below (branches uniform over the warp).
 #pragma unroll 1
     for (int k = 0; k < nc; k++) {
+        const bool shear = (k >= 2 && k < last);
+        const int tk = shear ? shear_axis<ND, D>(k) : 0;
         double lrow[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) {
@@ -299,6 +304,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
             const double Pc = cp + cm, Qc = cp - cm;
 #pragma unroll
             for (int c = 0; c < nc; c++) {
+                if (shear && c != 0 && c != 1 + tk) continue;
                 A[c] = fma(Qc, SQ(SL::QU + c, fo + j, p), A[c]);
                 B[c] = fma(Pc, SQ(SL::QF + c, fo + j, p), B[c]);
             }
@@ -308,19 +314,20 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         double wq = lrow[0] * A[0], gp = lrow[0] * B[0];
 #pragma unroll
         for (int c = 1; c < nc; c++) {
+            if (shear && c != 1 + tk) continue;
             wq = fma(lrow[c], A[c], wq);
             gp = fma(lrow[c], B[c], gp);
         }
         const double hk = fma(alpha, wq, gp);
         double Lb[nc];
 #pragma unroll
-        for (int c = 0; c < nc; c++) Lb[c] = fma(alpha, A[c], B[c]);
+        for (int c = 0; c < nc; c++) Lb[c] = (shear && c != 0) ? 0.0 : fma(alpha, A[c], B[c]);
         double ab = hbk * wq;
 #pragma unroll
         for (int kk = 0; kk < nc; kk++)
             if (k == kk) alphab[kk] = ab;
 #pragma unroll
-        for (int c = 0; c < nc; c++) Lb[c] *= hbk;
+        for (int c = 0; c < nc; c++) Lb[c] = (shear && c != 0) ? 0.0 : Lb[c] * hbk;
 
         // R column k: Rb[c] = Fb_c h_k.
         if (k == 0) {
@@ -467,7 +474,9 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
 
     // Per stencil cell: adjoint of U through the projection rows, and of the
     // cell's physical flux (the primitive-variable parts follow).
-    double *out = a.slots + (size_t)flin * W * 2 * nc;
+    // slot (j, q) of this face: a.slots[(j 2nc + q) nfaces + flin]
+    double *out = a.slots + flin;
+    const int64_t fs = a.nfaces;
     // w_j = l.U_j and g_j enter h_k with weights alpha Q_j and P_j:
     // wb = (alpha hb_k / 2)(c+ - c-), gb = (hb_k / 2)(c+ + c-).
     double sw[nc], sg[nc];
@@ -488,16 +497,19 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
             const double cm = frozen_coef<H>(fl[2 * k + 1], W - 1 - j);
             const double wb = sw[k] * (cp - cm);
             const double gb = sg[k] * (cp + cm);
+            const bool shear = (k >= 2 && k < last);
+            const int tk = shear ? shear_axis<ND, D>(k) : 0;
 #pragma unroll
             for (int c = 0; c < nc; c++) {
+                if (shear && c != 0 && c != 1 + tk) continue;    // zeros of a shear row
                 Ub[c] = fma(Lm[k][c], wb, Ub[c]);
                 Fcb[c] = fma(Lm[k][c], gb, Fcb[c]);
             }
         }
 #pragma unroll
         for (int c = 0; c < nc; c++) {
-            out[j * 2 * nc + c] = Ub[c];
-            out[j * 2 * nc + nc + c] = Fcb[c];
+            out[(j * 2 * nc + c) * fs] = Ub[c];
+            out[(j * 2 * nc + nc + c) * fs] = Fcb[c];
         }
     }
 
@@ -542,7 +554,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
                          SQ(SL::QSR, fo + je, p), SQ(SL::QRI, fo + je, p), ue, ce, He, se,
                          gamma, gm1, Ub);
 #pragma unroll
-        for (int c = 0; c < nc; c++) out[je * 2 * nc + c] += Ub[c];
+        for (int c = 0; c < nc; c++) out[(je * 2 * nc + c) * fs] += Ub[c];
     }
 #undef SQ
 }
@@ -596,9 +608,12 @@ __global__ void adj_gather_kernel(AdjArgs a, double *mu, int accumulate)
                 if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
                 else if (D == 1) flin = x + n0 * (f + (n1 + 1) * z);
                 else flin = x + n0 * (y + n1 * f);
-                const double *sl = a.slots + ((size_t)flin * W + j) * 2 * nc;
+                const double *sl = a.slots + (size_t)j * 2 * nc * a.nfaces + flin;
 #pragma unroll
-                for (int c = 0; c < nc; c++) { Us[c] += sl[c]; Fm[c] += sl[nc + c]; }
+                for (int c = 0; c < nc; c++) {
+                    Us[c] += sl[c * a.nfaces];
+                    Fm[c] += sl[(nc + c) * a.nfaces];
+                }
             }
             if (!ms[q]) {
 #pragma unroll

@@ -41,7 +41,11 @@ extern "C" {
 #define TENO_EINVAL 1          /* bad parameter, pointer, size or alignment   */
 #define TENO_ECUDA 2           /* a CUDA runtime call failed                  */
 #define TENO_ENONPHYSICAL 3    /* teno_status: non-physical states were seen  */
-#define TENO_ETIMEOUT 4        /* a bounded device-side wait gave up          */
+#define TENO_ETIMEOUT 4        /* reserved for a bounded device-side wait that
+                                  gave up; no call returns it: no kernel of
+                                  this library waits on a flag, a peer or a
+                                  barrier outside its own block (the batched
+                                  work list is an atomic counter)             */
 
 /* Boundary conditions per axis side (App. A). */
 #define TENO_BC_PERIODIC 0     /* App. A.4: ghost -r = cell n-r (both sides)  */

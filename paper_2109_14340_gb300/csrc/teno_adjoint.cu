@@ -56,7 +56,7 @@ constexpr size_t adj_smem_bytes()
 // Reverse of cell_quantities for the primitive outputs: adjoints of the
 // velocity ub, sound speed cb, enthalpy Hb and sqrt(rho) sb -> adjoint of U
 // (added into Ub); cinv = 1/c and rinv = 1/rho as staged.
-template <int ND>
+template <int ND, bool FULL = true>
 __device__ __forceinline__ void prim_adjoint(const double (&Uc)[ND + 2], const double (&u)[ND],
                                              double p, double cinv, double sr, double rinv,
                                              const double (&ub_in)[ND], double cb, double Hb,
@@ -72,10 +72,14 @@ __device__ __forceinline__ void prim_adjoint(const double (&Uc)[ND + 2], const d
     double rb = 0.0, Eb = 0.0, mb[ND];
 #pragma unroll
     for (int a = 0; a < ND; a++) mb[a] = 0.0;
-    rb += sb * 0.5 * (sr * rinv);                // sr = sqrt(rho): 1/sr = sr rinv
-    double Epb = Hb * rinv, rinvb = Hb * Ep;     // H = Ep rinv
-    Eb += Epb;                                   // Ep = E + p
-    double pb = Epb;
+    double pb = 0.0, rinvb = 0.0;
+    if (FULL) {                                  // (FULL = false: Hb = sb = 0)
+        rb += sb * 0.5 * (sr * rinv);            // sr = sqrt(rho): 1/sr = sr rinv
+        const double Epb = Hb * rinv;            // H = Ep rinv
+        rinvb = Hb * Ep;
+        Eb += Epb;                               // Ep = E + p
+        pb = Epb;
+    }
     const double zb = cb * 0.5 * cinv;           // c = sqrt(gamma p rinv)
     pb += gamma * rinv * zb;
     rinvb += gamma * p * zb;
@@ -550,9 +554,14 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         for (int c = 0; c < nc; c++) { Uc[c] = SQ(SL::QU + c, fo + je, p); Ub[c] = 0.0; }
 #pragma unroll
         for (int aa = 0; aa < ND; aa++) u[aa] = SQ(SL::QV + aa, fo + je, p);
-        prim_adjoint<ND>(Uc, u, SQ(SL::QP, fo + je, p), SQ(SL::QCI, fo + je, p),
-                         SQ(SL::QSR, fo + je, p), SQ(SL::QRI, fo + je, p), ue, ce, He, se,
-                         gamma, gm1, Ub);
+        if (e < 2)
+            prim_adjoint<ND, true>(Uc, u, SQ(SL::QP, fo + je, p), SQ(SL::QCI, fo + je, p),
+                                   SQ(SL::QSR, fo + je, p), SQ(SL::QRI, fo + je, p), ue, ce, He,
+                                   se, gamma, gm1, Ub);
+        else                                     // splitting speeds: u_D and c only
+            prim_adjoint<ND, false>(Uc, u, SQ(SL::QP, fo + je, p), SQ(SL::QCI, fo + je, p),
+                                    SQ(SL::QSR, fo + je, p), SQ(SL::QRI, fo + je, p), ue, ce, He,
+                                    se, gamma, gm1, Ub);
 #pragma unroll
         for (int c = 0; c < nc; c++) out[(je * 2 * nc + c) * fs] += Ub[c];
     }
@@ -650,8 +659,8 @@ __global__ void axpby_kernel(int64_t len, double a, const double *x, double b, c
 template <int ND, int H, int D>
 cudaError_t launch_adj_direction(const AdjArgs &a, double *mu, int accumulate, cudaStream_t s)
 {
-    constexpr int TP = (ND == 1) ? 1 : 8;
-    constexpr int TF = (ND == 1) ? 64 : 16;
+    constexpr int TP = (ND == 1) ? 1 : 4;
+    constexpr int TF = (ND == 1) ? 64 : 32;
     constexpr size_t smem = adj_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;
     if (!attr_done) {

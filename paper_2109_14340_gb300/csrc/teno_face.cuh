@@ -123,7 +123,8 @@ struct SmemLayout {
 //   memory each) beat two by 8-9 % and four by 9 %; with face n of periodic
 //   lines left out (256 faces per line), 4 x 32 beats 8 x 16 and 16 x 8 by
 //   0.5 % and 3 % (TENO10) and stages fewer halo cells per face;
-//   2D 512^2 TENO8: 4 x 32 ahead of 8 x 16 by 4 %.
+//   2D 512^2 TENO8: 4 x 32 ahead of 8 x 16 by 4 %, three blocks per SM
+//   ahead of an unbounded allocation by 3 %.
 // TENO_FACE_TP/TF/QCAP/MINB, when defined, override every case (tuning).
 template <int ND, int H>
 struct FaceTile {
@@ -136,7 +137,7 @@ struct FaceTile {
     static constexpr int TP = ND == 1 ? 1 : 4;
     static constexpr int TF = ND == 1 ? 128 : 32;
     static constexpr int QCAP = 2;
-    static constexpr int MINB = ND == 3 ? 3 : 1;
+    static constexpr int MINB = ND >= 2 ? 3 : 1;
 #endif
 };
 

@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-noh", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint workload and print its record (profiling)")
     ap.add_argument("--adjoint-n", type=int, default=512)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -717,6 +719,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.adjoint_only:
+        import torch
+        from paper_2109_14340_gb300 import _build
+        _build.build()
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps(run_adjoint(args, dev, torch.cuda.current_stream(dev))), flush=True)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -201,7 +201,7 @@ int teno_batch_workspace_bytes(const teno_batch *b, size_t *bytes);
 
 /* Autotuner: times one step (TENO_BATCH_STREAM) of every candidate tile width
  * (64/128/256 faces, i.e. 2/4/8 warps per pencil tile) and persistent grid size
- * (1/2/4 blocks per SM) on U_scratch (advanced in place: pass a copy) and keeps
+ * (1/2/3/4/6 blocks per SM) on U_scratch (advanced in place: pass a copy) and keeps
  * the fastest in the plan.  Results do not depend on the choice.
  * *chosen_tile and *chosen_blocks_per_sm (nullable) report it. */
 int teno_batch_autotune(teno_batch *b, double *U_scratch, void *ws, size_t ws_bytes,

@@ -95,8 +95,9 @@ __global__ void batch_finalize_kernel(const BatchProb *probs, int nprob, BatchSl
     slots[p].amax = 0ull;
 }
 
+// Registers bounded as for the 2D/3D sweeps: 384 threads' worth of blocks per SM.
 template <int TF>
-__global__ void __launch_bounds__(TF) batch_face_kernel(
+__global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_kernel(
     const BatchProb *probs, int nprob, const int32_t *fprefix, const double *U, double *F,
     BatchSlot *slots, Status *st, Consts K, FastK FK, int fast, int *counter)
 {
@@ -496,9 +497,9 @@ int teno_batch_autotune(teno_batch *b, double *U_scratch, void *ws, size_t ws_by
     CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_t = b->tile_idx, best_b = b->blocks_per_sm;
-    const int bps_c[3] = {1, 2, 4};
+    const int bps_c[5] = {1, 2, 3, 4, 6};
     for (int ti = 0; ti < 3; ti++) {
-        for (int bi = 0; bi < 3; bi++) {
+        for (int bi = 0; bi < 5; bi++) {
             int maxb = 0;
             const int TF = kTiles[ti];
             cudaError_t oe;

@@ -37,8 +37,8 @@ struct CombineArgs {
 };
 
 // L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. approximateEq), then the
-// SSP-RK3 stage combination (Eq. Runge-kutta); counts non-physical cells of
-// the stage input.
+// SSP-RK3 stage combination (Eq. Runge-kutta).  The stage input's
+// non-physical cells are counted by the x sweep, which stages every cell.
 template <int ND>
 __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
 {
@@ -57,21 +57,6 @@ __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
     double Uc[nc];
 #pragma unroll
     for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
-    {
-        // the non-physical test of cell_quantities: rho > 0, p > 0, c and H
-        // finite (c = sqrt(gamma p / rho) is finite exactly when its
-        // argument is, for p > 0)
-        const double rho = Uc[0], E = Uc[nc - 1];
-        const double rinv = 1.0 / rho;
-        double t = Uc[1] * (Uc[1] * rinv);
-#pragma unroll
-        for (int k = 1; k < ND; k++) t = fma(Uc[1 + k], Uc[1 + k] * rinv, t);
-        const double p = a.K.gm1 * (E - 0.5 * t);
-        const double c2 = (a.K.gamma * p) * rinv;
-        const double Hc = (E + p) * rinv;
-        if (!(rho > 0.0) || !(p > 0.0) || !isfinite(c2) || !isfinite(Hc))
-            atomicAdd(&a.st->nonphys, 1ull);
-    }
     const double dt = a.st->dt;
 #pragma unroll
     for (int c = 0; c < nc; c++) {
@@ -394,6 +379,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.lam = &st->lam[d];
         a.fast = g_fast_filter;
         a.skip_last = (p->bc_lo[d] == TENO_BC_PERIODIC && !fl && !fz) ? 1 : 0;
+        a.count_cells = (d == 0);                 // the x sweep counts the stage input's cells
         a.exact_count = g_prof.on ? g_prof.exact : nullptr;
         a.FK = fastk_of(p);
         a.K = K;

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         a.lam = &slots[p].lam;
         a.fast = fast;
         a.skip_last = 0;
+        a.count_cells = 0;
         a.exact_count = nullptr;
         a.FK = FK;
         a.K = K;

@@ -29,6 +29,8 @@ struct FaceArgs {
     const double *bcs_lo, *bcs_hi;   // Dirichlet boundary-face states of axis D, or nullptr
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
+    int count_cells;       // 1: count the non-physical cells this sweep owns (one
+                           // sweep per evaluation does, so each cell is counted once)
     int skip_last;         // 1: face n of each line is not computed (periodic axis, no
                            // decision record: its flux is face 0's, bitwise)
     unsigned long long *exact_count;   // adds the exact-path reconstructions, or nullptr
@@ -194,6 +196,13 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         }
         CellQ<ND> q;
         cell_quantities<ND, D>(Uc, a.K, q);
+        if (a.count_cells) {
+            // interior cells of this tile's own face range: each cell once
+            const int64_t ci = f0 - H + j;
+            if (ci >= f0 && ci < f0 + TF && ci < nD &&
+                (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H)))
+                atomicAdd(&a.st->nonphys, 1ull);
+        }
 #pragma unroll
         for (int c = 0; c < nc; c++) { SQ(SL::QU + c, j, p) = q.U[c]; SQ(SL::QF + c, j, p) = q.F[c]; }
 #pragma unroll

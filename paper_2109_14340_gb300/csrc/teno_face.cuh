@@ -121,12 +121,13 @@ struct SmemLayout {
 // queue's capacity in reconstructions per thread (QCAP) and the blocks per SM
 // the register allocation is bounded for (MINB).  A single line (1D) uses
 // 1 x 128.  Measured on GB300 with 128-thread blocks:
-//   3D 256^3: three blocks per SM (168 registers, about 60 KB of shared
-//   memory each) beat two by 8-9 % and four by 9 %; with face n of periodic
+//   3D 256^3: TENO10 at three blocks per SM (164 registers, about 60 KB of
+//   shared memory each) beats two by 8-9 % and four by 6 %; TENO8 at four
+//   (128 registers) beats three by 2 %; with face n of periodic
 //   lines left out (256 faces per line), 4 x 32 beats 8 x 16 and 16 x 8 by
 //   0.5 % and 3 % (TENO10) and stages fewer halo cells per face;
-//   2D 512^2 TENO8: 4 x 32 ahead of 8 x 16 by 4 %, three blocks per SM
-//   ahead of an unbounded allocation by 3 %.
+//   2D 512^2 TENO8: 4 x 32 ahead of 8 x 16 by 4 %, a register bound (three
+//   or four blocks per SM) ahead of an unbounded allocation by 3 %.
 // TENO_FACE_TP/TF/QCAP/MINB, when defined, override every case (tuning).
 template <int ND, int H>
 struct FaceTile {
@@ -139,7 +140,7 @@ struct FaceTile {
     static constexpr int TP = ND == 1 ? 1 : 4;
     static constexpr int TF = ND == 1 ? 128 : 32;
     static constexpr int QCAP = 2;
-    static constexpr int MINB = ND >= 2 ? 3 : 1;
+    static constexpr int MINB = ND >= 2 ? (H == 4 ? 4 : 3) : 1;
 #endif
 };
 
@@ -230,7 +231,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     // decision byte already in the owner's Qfl slot).
     constexpr int CAP = FaceTile<ND, H>::QCAP * TP * TF, QE = CAP / 4;
     double *Qv = sm + (size_t)SL::NQ * NS * TP;       // [CAP][W]
-    double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]
+    double *Qres = Qv + (size_t)CAP * W;              // [threads][2 nc]: every value of the face
     int *Qmeta = (int *)(Qres + (size_t)TP * TF * 2 * nc);   // [CAP]
     uint8_t *Qfl = (uint8_t *)(Qmeta + CAP);          // [threads][2 nc]
 
@@ -275,10 +276,9 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     // is full, done in place) and drained once per tile by the whole block --
     // the undecided ones with the exact path, the decided ones (fallback or a
     // smaller stencil) with their value formula, so that neither diverges
-    // inside a warp.
-    double hv[2 * nc];                 // the two reconstructed values per field
-#pragma unroll
-    for (int q = 0; q < 2 * nc; q++) hv[q] = 0.0;
+    // inside a warp.  Each value lands in the owner's Qres slot (shared
+    // memory, not registers: 2 nc values held there would stay live across
+    // the whole field loop and push the kernel into spills).
     unsigned pending = 0;              // bit 2k+s: value comes from the queue
 #pragma unroll 1
     for (int k = 0; k < nc; k++) {
@@ -352,9 +352,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 }
             }
             if (done) {
-#pragma unroll
-                for (int q = 0; q < 2 * nc; q++)
-                    if (q == 2 * k + s) hv[q] = val;
+                Qres[threadIdx.x * (2 * nc) + 2 * k + s] = val;
                 if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
             }
         }
@@ -387,7 +385,6 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #pragma unroll
             for (int q = 0; q < 2 * nc; q++) {
                 if (pending & (1u << q)) {
-                    hv[q] = Qres[threadIdx.x * (2 * nc) + q];
                     if (a.flags) a.flags[(flin * nc + (q >> 1)) * 2 + (q & 1)] = Qfl[threadIdx.x * (2 * nc) + q];
                 }
             }
@@ -400,7 +397,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
     if (active) {
 #pragma unroll
         for (int k = 0; k < nc; k++) {
-            const double hsum = hv[2 * k] + hv[2 * k + 1];
+            const double hsum = Qres[threadIdx.x * (2 * nc) + 2 * k] + Qres[threadIdx.x * (2 * nc) + 2 * k + 1];
             if (k == 0) {
 #pragma unroll
                 for (int c = 0; c < nc; c++) Fo[c] = r_entry<ND, D>(rs, c, 0) * hsum;

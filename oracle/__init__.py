@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "teno_oracle.c")
+_TABLES = os.path.join(_HERE, "teno12_tables.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libteno_oracle.so")
 _lock = threading.Lock()
@@ -33,7 +34,8 @@ SPLIT_LLF, SPLIT_RUSANOV = 0, 1
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, IEEE division/sqrt)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_TABLES))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".%d.tmp" % os.getpid()
         cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
                "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
@@ -118,6 +120,8 @@ def _load():
             lib.oracle_round_ratio.restype = ctypes.c_double
             lib.oracle_beta_coef.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_beta_coef.restype = ctypes.c_double
+            lib.oracle_lin_coef.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.oracle_lin_coef.restype = ctypes.c_double
             ci = ctypes.POINTER(ctypes.c_int)
             cs = ctypes.POINTER(ctypes.c_char_p)
             lib.oracle_beta_terms.argtypes = [ctypes.c_int, ctypes.c_int, ci, ci, cs, cs]
@@ -228,11 +232,16 @@ def rhs_at(p: Params, U, cells, dt_lim: float = 0.0, threads: int = 1):
     return out
 
 
+def half_width(p: Params) -> int:
+    """H = 4, 5, 6 for TENO8, TENO10, TENO12-AA."""
+    return {8: 4, 10: 5, 12: 6}[p.scheme]
+
+
 def recon(p: Params, v):
     """Scalar TENO-AA reconstruction at face i+1/2 from v at offsets -H+1..H.
     Returns (value, flag byte)."""
     lib = _load()
-    H = 5 if p.scheme == 10 else 4
+    H = half_width(p)
     v = np.ascontiguousarray(v, np.float64)
     assert v.size == 2 * H
     fl = np.zeros(1, np.uint8)
@@ -257,7 +266,9 @@ def round_ratio(num: int, den: int) -> float:
 
 def beta_terms(width: int):
     """The printed integer terms (a, b, coefficient) and denominator of the
-    width-point smoothness indicator, as the oracle transcribed them."""
+    width-point smoothness indicator (6, 8, 10), as the oracle transcribed
+    them."""
+    assert width in (6, 8, 10)
     lib = _load()
     a, b = ctypes.c_int(), ctypes.c_int()
     c, den = ctypes.c_char_p(), ctypes.c_char_p()
@@ -271,14 +282,40 @@ def beta_terms(width: int):
     return terms, int(den.value.decode())
 
 
-def betas(p: Params, v):
-    """(beta_0..beta_5, fhat_0..fhat_5) of one stencil v at offsets -H+1..H."""
+def beta_fractions(width: int):
+    """Terms (a, b, Fraction) of the width-point indicator as the oracle
+    holds them: the printed ones (6, 8, 10) or the derived beta_{6,12}."""
+    from fractions import Fraction
+    if width != 12:
+        terms, den = beta_terms(width)
+        return [(a, b, Fraction(c, den)) for a, b, c in terms]
     lib = _load()
-    H = 5 if p.scheme == 10 else 4
+    a, b = ctypes.c_int(), ctypes.c_int()
+    c, den = ctypes.c_char_p(), ctypes.c_char_p()
+    nt = lib.oracle_beta_terms(12, -1, ctypes.byref(a), ctypes.byref(b),
+                               ctypes.byref(c), ctypes.byref(den))
+    out = []
+    for i in range(nt):
+        lib.oracle_beta_terms(12, i, ctypes.byref(a), ctypes.byref(b),
+                              ctypes.byref(c), ctypes.byref(den))
+        out.append((a.value, b.value, Fraction(int(c.value.decode()), int(den.value.decode()))))
+    return out
+
+
+def lin_coef(L: int, off: int) -> float:
+    """Coefficient of the large stencil S_L's linear scheme at offset off."""
+    return _load().oracle_lin_coef(L, off)
+
+
+def betas(p: Params, v):
+    """(beta_0..beta_6, fhat_0..fhat_6) of one stencil v at offsets -H+1..H
+    (entries above L = H are zero)."""
+    lib = _load()
+    H = half_width(p)
     v = np.ascontiguousarray(v, np.float64)
     assert v.size == 2 * H
-    b = np.zeros(6)
-    f = np.zeros(6)
+    b = np.zeros(7)
+    f = np.zeros(7)
     lib.oracle_betas(ctypes.byref(p), _dp(v), _dp(b), _dp(f))
     return b, f
 
@@ -288,8 +325,10 @@ def beta_coef(width: int, r: int, s: int) -> float:
 
 
 def decode_flag(fl: int):
-    """(selected large stencil 3|4|5 or 0 for the small-stencil fallback,
-    (delta0, delta1, delta2), C_T exponent)."""
+    """(selected large stencil 3|4|5|6 or 0 for the small-stencil fallback,
+    (delta0, delta1, delta2), C_T exponent).  Bits 0-4 all zero mean S6."""
     sel = fl & 3
-    return (sel + 2 if sel else 0, ((fl >> 2) & 1, (fl >> 3) & 1, (fl >> 4) & 1),
-            ((fl >> 5) & 7) + 7)
+    ct = ((fl >> 5) & 7) + 7
+    if (fl & 31) == 0:
+        return 6, (0, 0, 0), ct
+    return (sel + 2 if sel else 0, ((fl >> 2) & 1, (fl >> 3) & 1, (fl >> 4) & 1), ct)

@@ -1,7 +1,7 @@
 /*
  * TENO-AA CPU oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow FP64 restatement of the eight- and ten-point TENO-AA schemes of
+ * A plain, slow FP64 restatement of the eight-, ten- and twelve-point TENO-AA schemes of
  * L. Fu, "Very-high-order TENO schemes with adaptive accuracy order and adaptive
  * dissipation control" (arXiv 2109.14340), applied to the compressible Euler
  * equations (Sec. 1, Eq. Euler) in the conservative finite-difference form of
@@ -9,8 +9,11 @@
  *
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
  * load this library.  It shares no code with the CUDA path: its coefficient
- * tables are its own transcription of Sec. 4, and every step is recomputed per
- * face from the conserved variables, in the order the paper states it.
+ * tables are its own transcription of Sec. 4 (the twelve-point candidate S6,
+ * which the paper does not print, comes from oracle/teno12_derive.py, the
+ * oracle's own derivation by the Sec. 4.1 recipe), and every step is
+ * recomputed per face from the conserved variables, in the order the paper
+ * states it.
  *
  * Rounding is pinned: build with -ffp-contract=off; the only fused operations
  * are the explicit fma() calls (dot products and quadratic forms).  Division and
@@ -32,7 +35,7 @@
 #endif
 
 #define MAXC 5          /* conserved variables in 3D: rho, m_x, m_y, m_z, E */
-#define MAXH 5          /* half-width of the ten-point stencil                */
+#define MAXH 6          /* half-width of the twelve-point stencil             */
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_SLIPWALL = 2, BC_NOSLIP = 3, BC_DIRICHLET = 4 };
 enum { SPLIT_LLF = 0, SPLIT_RUSANOV = 1 };
@@ -142,6 +145,13 @@ static const qterm B510[] = {
     {-4, -4, "18029727887840089"},
 };
 
+/* The twelve-point candidate S6 (TENO12-AA): terms of beta_{6,12} as reduced
+ * fractions (offset a, offset b, numerator, denominator) and the linear scheme
+ * LIN6, both derived by oracle/teno12_derive.py from Eq. measureTENO and the
+ * optimisation of Sec. 4.1. */
+typedef struct { int a, b; const char *c, *d; } qterm2;
+#include "teno12_tables.h"
+
 /* Quadratic-form coefficient c/D rounded to the nearest double (ties to even),
  * computed exactly with 128-bit integers. */
 typedef __int128 i128;
@@ -189,7 +199,7 @@ double oracle_round_ratio(const char *num, const char *den)
 }
 
 /* Upper-triangular coefficient matrices, rows and columns in ascending offset. */
-static double Q36[6][6], Q48[8][8], Q510[10][10];
+static double Q36[6][6], Q48[8][8], Q510[10][10], Q612[12][12];
 static int tables_ready = 0;
 
 static void fill_table(const qterm *t, int nt, const char *den, int lo, int w, double *M)
@@ -211,16 +221,30 @@ static void init_tables(void)
             fill_table(B36, sizeof(B36) / sizeof(B36[0]), B36_DEN, -2, 6, &Q36[0][0]);
             fill_table(B48, sizeof(B48) / sizeof(B48[0]), B48_DEN, -3, 8, &Q48[0][0]);
             fill_table(B510, sizeof(B510) / sizeof(B510[0]), B510_DEN, -4, 10, &Q510[0][0]);
+            memset(Q612, 0, sizeof(Q612));
+            for (size_t e = 0; e < sizeof(B612) / sizeof(B612[0]); e++) {
+                int r = B612[e].a < B612[e].b ? B612[e].a : B612[e].b;
+                int c = B612[e].a < B612[e].b ? B612[e].b : B612[e].a;
+                Q612[r + 5][c + 5] = oracle_round_ratio(B612[e].c, B612[e].d);
+            }
             tables_ready = 1;
         }
     }
 }
 
-/* Exposed for the coefficient pins: the integer terms of one indicator. */
+/* Exposed for the coefficient pins: the integer terms of one indicator (for
+ * width 12 each term carries its own denominator). */
 int oracle_beta_terms(int width, int idx, int *a, int *b, const char **c, const char **den)
 {
     const qterm *t;
     int nt;
+    if (width == 12) {
+        nt = (int)(sizeof(B612) / sizeof(B612[0]));
+        if (idx < 0) return nt;
+        if (idx >= nt) return -1;
+        *a = B612[idx].a; *b = B612[idx].b; *c = B612[idx].c; *den = B612[idx].d;
+        return nt;
+    }
     if (width == 6) { t = B36; nt = sizeof(B36) / sizeof(B36[0]); *den = B36_DEN; }
     else if (width == 8) { t = B48; nt = sizeof(B48) / sizeof(B48[0]); *den = B48_DEN; }
     else if (width == 10) { t = B510; nt = sizeof(B510) / sizeof(B510[0]); *den = B510_DEN; }
@@ -231,14 +255,33 @@ int oracle_beta_terms(int width, int idx, int *a, int *b, const char **c, const 
     return nt;
 }
 
-/* Table coefficient (rounded double) for the pins: width 6/8/10, offsets r<=s. */
+/* Table coefficient (rounded double) for the pins: width 6/8/10/12, offsets r<=s. */
 double oracle_beta_coef(int width, int r, int s)
 {
     init_tables();
     if (r > s) { int t = r; r = s; s = t; }
     if (width == 6) return Q36[r + 2][s + 2];
     if (width == 8) return Q48[r + 3][s + 3];
+    if (width == 12) return Q612[r + 5][s + 5];
     return Q510[r + 4][s + 4];
+}
+
+/* Linear-scheme coefficient of S_L at offset off (0 outside the stencil). */
+double oracle_lin_coef(int L, int off)
+{
+    switch (L) {
+    case 3: return (off >= -2 && off <= 3) ? LIN3[off + 2] : 0.0;
+    case 4: return (off >= -3 && off <= 4) ? LIN4[off + 3] : 0.0;
+    case 5: return (off >= -4 && off <= 5) ? LIN5[off + 4] : 0.0;
+    case 6: return (off >= -5 && off <= 6) ? LIN6[off + 5] : 0.0;
+    default: return 0.0;
+    }
+}
+
+/* Half-width H of the scheme: 4, 5, 6 for TENO8, TENO10, TENO12-AA. */
+static int half_width(const or_params *P)
+{
+    return P->scheme == 12 ? 6 : (P->scheme == 10 ? 5 : 4);
 }
 
 /* Powers of ten for C_T = 10^-[beta] (Eq. CT_definition). */
@@ -256,13 +299,14 @@ static const double TENPOW[23] = {
  * the shift leaves it unchanged and removes the constant's cancellation). */
 static double beta_large(int L, const double *v, int H)
 {
-    int lo = -(L - 1) + 0;              /* S3: -2..3, S4: -3..4, S5: -4..5 */
+    int lo;                             /* S3: -2..3, S4: -3..4, S5: -4..5, S6: -5..6 */
     int w;
     const double *M;
     if (L == 3) { lo = -2; w = 6; M = &Q36[0][0]; }
     else if (L == 4) { lo = -3; w = 8; M = &Q48[0][0]; }
-    else { lo = -4; w = 10; M = &Q510[0][0]; }
-    double s[10];
+    else if (L == 5) { lo = -4; w = 10; M = &Q510[0][0]; }
+    else { lo = -5; w = 12; M = &Q612[0][0]; }
+    double s[12];
     double v0 = v[H - 1];
     for (int r = 0; r < w; r++) s[r] = v[lo + r + H - 1] - v0;
     double acc = 0.0;
@@ -274,14 +318,15 @@ static double beta_large(int L, const double *v, int H)
     return acc;
 }
 
-/* Linear scheme of the large stencil S_L (Eqs. 6-, 8-, 10-point). */
+/* Linear scheme of the large stencil S_L (Eqs. 6-, 8-, 10-point; S6 derived). */
 static double flux_large(int L, const double *v, int H)
 {
     int lo, w;
     const double *c;
     if (L == 3) { lo = -2; w = 6; c = LIN3; }
     else if (L == 4) { lo = -3; w = 8; c = LIN4; }
-    else { lo = -4; w = 10; c = LIN5; }
+    else if (L == 5) { lo = -4; w = 10; c = LIN5; }
+    else { lo = -5; w = 12; c = LIN6; }
     double acc = c[0] * v[lo + H - 1];
     for (int r = 1; r < w; r++) acc = fma(c[r], v[lo + r + H - 1], acc);
     return acc;
@@ -326,11 +371,13 @@ static int ct_exponent(const or_params *P, const double *v, int H)
 
 /* One TENO-AA reconstruction.  flag: bits 0-1 selected large stencil (L-2) or
  * 0 for the small-stencil fallback, bits 2-4 cut-off deltas of S0..S2 (fallback
- * only), bits 5-7 C_T exponent minus 7. */
+ * only), bits 5-7 C_T exponent minus 7.  S6 (twelve-point scheme) is written
+ * with bits 0-4 all zero: a fallback always keeps at least one small stencil
+ * (the three chi_k sum to one), so that pattern is otherwise unused. */
 double oracle_teno_recon(const or_params *P, const double *v, uint8_t *flag)
 {
     init_tables();
-    int p = P->scheme == 10 ? 5 : 4;
+    int p = half_width(P);
     int H = p;
 #define V(m) v[(m) + H - 1]
     int nexp = ct_exponent(P, v, H);
@@ -357,7 +404,7 @@ double oracle_teno_recon(const or_params *P, const double *v, uint8_t *flag)
         double sum = ((g0 + g1) + g2) + gL;
         double chi = gL / sum;                   /* Eq. normalize */
         if (!(chi < CT)) {                       /* Eq. cutoff: delta = 1 */
-            *flag = (uint8_t)((L - 2) | fct);
+            *flag = (uint8_t)((L == 6 ? 0 : L - 2) | fct);
             return flux_large(L, v, H);
         }
     }
@@ -601,7 +648,7 @@ static void face_flux(const or_params *P, int d, const cellq *st, const lim_info
                       double *Fout, uint8_t *flags, int *bad_face, int *lim_on)
 {
     int nd = P->ndim, nc = nd + 2;
-    int H = P->scheme == 10 ? 5 : 4, W = 2 * H;
+    int H = half_width(P), W = 2 * H;
     const cellq *cl = &st[H - 1], *cr = &st[H];
     int last = nc - 1;
 
@@ -754,7 +801,7 @@ int64_t oracle_rhs(const or_params *P, const double *U, double *rhs, double dt_l
 {
     init_tables();
     int nd = P->ndim, nc = nd + 2;
-    int H = P->scheme == 10 ? 5 : 4, W = 2 * H;
+    int H = half_width(P), W = 2 * H;
     int64_t N = ncells(P);
     double lam[3] = {0.0, 0.0, 0.0};
     if (P->limiter) lim_lambdas(P, U, dt_lim, lam);
@@ -873,7 +920,7 @@ void oracle_rhs_at(const or_params *P, const double *U, const int64_t *cells, in
 {
     init_tables();
     int nd = P->ndim, nc = nd + 2;
-    int H = P->scheme == 10 ? 5 : 4, W = 2 * H;
+    int H = half_width(P), W = 2 * H;
     double lam[3] = {0.0, 0.0, 0.0};
     if (P->limiter) lim_lambdas(P, U, dt_lim, lam);
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
@@ -927,12 +974,12 @@ int oracle_max_threads(void)
 #endif
 }
 
-/* Pins: the six smoothness indicators beta_0..beta_5 (beta_5 only for the
- * ten-point scheme) and the six candidate fluxes f_0..f_5 of one stencil. */
+/* Pins: the seven smoothness indicators beta_0..beta_6 (beta_L only for
+ * L <= H) and the seven candidate fluxes f_0..f_6 of one stencil. */
 void oracle_betas(const or_params *P, const double *v, double *beta, double *fhat)
 {
     init_tables();
-    int p = P->scheme == 10 ? 5 : 4;
+    int p = half_width(P);
     int H = p;
 #define V(m) v[(m) + H - 1]
     double a0 = V(-1) - V(1);
@@ -947,7 +994,7 @@ void oracle_betas(const or_params *P, const double *v, double *beta, double *fha
     fhat[0] = ((-V(-1) + 5.0 * V(0)) + 2.0 * V(1)) / 6.0;
     fhat[1] = ((2.0 * V(0) + 5.0 * V(1)) - V(2)) / 6.0;
     fhat[2] = ((2.0 * V(-2) - 7.0 * V(-1)) + 11.0 * V(0)) / 6.0;
-    for (int L = 3; L <= 5; L++) {
+    for (int L = 3; L <= 6; L++) {
         if (L > p) { beta[L] = 0.0; fhat[L] = 0.0; continue; }
         beta[L] = beta_large(L, v, H);
         fhat[L] = flux_large(L, v, H);

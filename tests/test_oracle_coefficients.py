@@ -103,7 +103,7 @@ def _exact_beta(Q, f):
     return float(sum(Q[a][b] * fr[a] * fr[b] for a in range(len(f)) for b in range(len(f))))
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_beta_evaluation_matches_exact(scheme):
     """The six indicators as evaluated by the oracle agree with the exact
     rational forms (small ones derived the same way from Eq. measureTENO)."""
@@ -115,8 +115,10 @@ def test_beta_evaluation_matches_exact(scheme):
              2: ([-2, -1, 0], smoothness_form([-2, -1, 0])),
              3: (STENCILS[6], smoothness_form(STENCILS[6])),
              4: (STENCILS[8], smoothness_form(STENCILS[8]))}
-    if scheme == 10:
+    if scheme >= 10:
         forms[5] = (STENCILS[10], smoothness_form(STENCILS[10]))
+    if scheme == 12:
+        forms[6] = (list(range(-5, 7)), smoothness_form(list(range(-5, 7))))
     g = np.random.Generator(np.random.PCG64(11))
     for trial in range(60):
         v = g.uniform(-1, 1, 2 * H) * (10.0 ** g.uniform(-3, 3))
@@ -138,14 +140,14 @@ def _cell_avgs(k, s, offs):
     return np.array([float(Fr(s) ** k * _cell_avg_monomial(j, k)) for j in offs])
 
 
-@pytest.mark.parametrize("L,order", [(0, 3), (1, 3), (2, 3), (3, 4), (4, 6), (5, 8)])
+@pytest.mark.parametrize("L,order", [(0, 3), (1, 3), (2, 3), (3, 4), (4, 6), (5, 8), (6, 10)])
 def test_candidate_flux_orders(L, order):
     """f_0..f_2 are third order, S3/S4/S5 are fourth/sixth/eighth order
-    (Sec. 4.1): exact at the face x = 1/2 for polynomials of degree < order,
-    and not for degree = order."""
-    scheme = 10
+    (Sec. 4.1), the derived S6 tenth: exact at the face x = 1/2 for
+    polynomials of degree < order, and not for degree = order."""
+    scheme = 12 if L == 6 else 10
     p = oracle.params(1, [16], [1.0], scheme=scheme)
-    offs = list(range(-4, 6))
+    offs = list(range(-scheme // 2 + 1, scheme // 2 + 1))
     s = Fr(1, 5)
     for k in range(order + 1):
         v = _cell_avgs(k, s, offs)
@@ -219,7 +221,7 @@ def test_ct_worked_example():
         assert ct == want, (t, ct)
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_selection_on_steps(scheme):
     """A unit step placed between offsets s-1 and s: the large stencils that
     straddle it are dropped (largest first) and the small-stencil cut-offs
@@ -233,11 +235,13 @@ def test_selection_on_steps(scheme):
         0: (0, (0, 1, 0)),       # step between -1 and 0: S0, S2 straddle
         -1: (0, (1, 1, 0)),      # step between -2 and -1: only S2 straddles
     }
-    if scheme == 10:
+    expect[-2] = (3, None)       # step between -3 and -2: S3 smooth, S4.. not
+    if scheme >= 10:
         expect[5] = (4, None)    # S4 = -3..4 smooth, S5 straddles
-        expect[-2] = (3, None)   # step between -3 and -2: S3 smooth, S4/S5 not
-    else:
-        expect[-2] = (3, None)
+        expect[-3] = (4, None)   # step between -4 and -3: S4 smooth
+    if scheme == 12:
+        expect[6] = (5, None)    # S5 = -4..5 smooth, S6 straddles
+        expect[-4] = (5, None)   # step between -5 and -4: S5 smooth
     for s, (sel_w, deltas) in expect.items():
         v = np.where(offs >= s, 1.0, 0.0)
         val, (sel, dl, ct) = _recon(scheme, v)
@@ -253,7 +257,7 @@ def test_selection_on_steps(scheme):
             assert val == pytest.approx(w @ fh[:3], rel=1e-15, abs=1e-15)
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_smooth_data_selects_largest(scheme):
     """Smooth data: the largest stencil is selected and the output is exactly
     its linear scheme (TENO reverts to the linear scheme, Sec. 3.3)."""

@@ -19,7 +19,8 @@ import riemann_exact
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("scheme,Ns,min_order", [(8, (20, 40, 80, 160), 5.7),
-                                                  (10, (10, 20, 40, 80), 7.5)])
+                                                  (10, (10, 20, 40, 80), 7.5),
+                                                  (12, (10, 20, 40), 9.5)])
 def test_design_order(scheme, Ns, min_order):
     errs = []
     for N in Ns:
@@ -96,7 +97,7 @@ LIN = {8: (-3, [-0.006866688980568011, 0.05128582585522106, -0.1968478198727312,
                  0.001832421220128962])}
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_linear_recovery_componentwise(scheme):
     """With one splitting speed for all fields (Rusanov) and the largest
     stencil selected everywhere, the characteristic-wise flux equals the
@@ -111,11 +112,15 @@ def test_linear_recovery_componentwise(scheme):
     p = oracle.params(1, [N], [1.0 / N], scheme=scheme, split=oracle.SPLIT_RUSANOV)
     r, fl, _, nb = oracle.rhs(p, U, want_flags=True)
     assert nb == 0
-    assert np.all((fl & 3) == scheme // 2 - 2)        # every face, field, sign: S_p
     H = scheme // 2
+    # every face, field, sign: S_p (S6 of TENO12 is written with bits 0-4 zero)
+    assert all(oracle.decode_flag(int(x))[0] == H for x in np.unique(fl))
     c = np.sqrt(gamma * pr / rho)
     F = _euler_flux(U, 0, gamma)
-    lo, co = LIN[scheme]
+    if scheme == 12:       # the derived S6, pinned in test_oracle_teno12.py
+        lo, co = -5, [oracle.lin_coef(6, m) for m in range(-5, 7)]
+    else:
+        lo, co = LIN[scheme]
     Ff = np.zeros((3, N + 1))
     for f in range(N + 1):                    # face between cells f-1 and f
         cells = [(f - H + j) % N for j in range(2 * H)]
@@ -141,7 +146,7 @@ def _uniform(ndim, n, vel, gamma=1.4):
 
 
 @pytest.mark.parametrize("ndim,n", [(1, [24]), (2, [16, 12]), (3, [10, 9, 8])])
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 @pytest.mark.parametrize("bc", [0, 1, 2])
 @pytest.mark.parametrize("limiter", [0, 1])
 def test_free_stream_bitwise(ndim, n, scheme, bc, limiter):
@@ -156,7 +161,7 @@ def test_free_stream_bitwise(ndim, n, scheme, bc, limiter):
 
 
 @pytest.mark.parametrize("ndim,n", [(1, [48]), (2, [20, 18]), (3, [12, 11, 10])])
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_conservation_periodic(ndim, n, scheme):
     """Periodic: the totals of the conserved variables change by rounding only
     over an RK3 step (the face fluxes telescope)."""
@@ -220,7 +225,7 @@ def _l1_density_error(case, Ns, threads=2):
     return errs
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_sod_converges(scheme):
     errs = _l1_density_error(lambda N: workloads.sod_1d(N, scheme), (50, 100, 200))
     assert errs[0] > errs[1] > errs[2]
@@ -236,7 +241,7 @@ def test_seeded_riemann_converges():
 # positivity-preserving limiter (Sec. 5.3)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_limiter_keeps_double_rarefaction_positive(scheme):
     c = workloads.double_rarefaction_1d(200, scheme)
     p = oracle_params(c, limiter=1)
@@ -298,7 +303,7 @@ def test_limiter_inactive_on_smooth_data(ndim):
 # symmetry and ghost cells (App. A)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_mirror_symmetry_1d(scheme):
     """x -> -x with u -> -u maps the RHS onto itself (momentum negated)."""
     g = np.random.Generator(np.random.PCG64(5))
@@ -315,7 +320,7 @@ def test_mirror_symmetry_1d(scheme):
     assert np.abs(back - r).max() <= 1e-12 * np.abs(r).max()
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_slip_wall_equals_mirrored_periodic(scheme):
     """Slip walls at both ends (App. A.1: ghost -r = cell r-1 with the normal
     velocity negated) give exactly the RHS of the periodic problem on the
@@ -376,7 +381,7 @@ def test_dimension_by_dimension():
     assert np.abs(r2 - r3).max() <= 1e-12 * np.abs(r2).max()
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_noslip_equals_mirrored_periodic(scheme):
     """No-slip walls in y (App. A.2: ghost -r = cell r-1 with every velocity
     component negated) give exactly the RHS of the y-periodic problem on the
@@ -399,7 +404,7 @@ def test_noslip_equals_mirrored_periodic(scheme):
     assert np.array_equal(r, r2[:, :nx * ny])
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_dirichlet_equals_padded_domain(scheme):
     """Dirichlet sides in y (App. A.3: the ghost's primitives are 2 phi' - phi
     of the mirror cell r-1) give exactly the RHS of a domain padded with those

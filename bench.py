@@ -7,7 +7,7 @@ and the stage combinations), all on the device, dt kept on the device.
 value = cell-updates/s over all ranks (each rank advances its own independent
 256^3 problem: weak scaling, no data-path collective).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme 8|10]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--scheme 8|10|12]
   python bench.py --impl reference      # the CPU oracle on the host cores
 
 Prints one JSON line on rank 0.
@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scheme", type=int, default=10, choices=[8, 10])
+    ap.add_argument("--scheme", type=int, default=10, choices=[8, 10, 12])
     ap.add_argument("--n", "--size", dest="n", type=int, default=256,
                     help="cells per axis of the 3D workload (--size under torchrun, whose "
                          "own options shadow --n)")
@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-noh", action="store_true")
+    ap.add_argument("--no-teno12", action="store_true",
+                    help="skip the TENO12-AA line (same workload, twelve-point scheme)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint workload and print its record (profiling)")
     ap.add_argument("--adjoint-n", type=int, default=512)
@@ -86,10 +88,20 @@ def beta_large_flops(w):
     return k + k * k + 2 * k - 1
 
 
-def recon_flops(H, flag):
-    """Algorithmic flops of one reconstruction given its decision byte."""
+def selection_class(flags_np, H):
+    """Per decision byte: L - 2 of the selected large stencil S_L (1..4) or 0
+    for the small-stencil fallback (S6 of the twelve-point scheme is written
+    with bits 0-4 zero)."""
+    import numpy as np
+    sel = (flags_np & 3).astype(np.int64)
+    if H == 6:
+        sel[(flags_np & 31) == 0] = 4
+    return sel
+
+
+def recon_flops(H, sel):
+    """Algorithmic flops of one reconstruction given its selection class."""
     base = 48 + 33 + 18 + 2            # C_T measure, small indicators, their gammas, sum
-    sel = flag & 3
     tested = []
     for L in range(H, 2, -1):
         tested.append(L)
@@ -107,10 +119,10 @@ def recon_flops(H, flag):
 
 def flops_per_face_from_flags(flags_np, nd, H):
     import numpy as np
-    hist = np.bincount(flags_np & 3, minlength=4).astype(np.float64)
+    hist = np.bincount(selection_class(flags_np, H), minlength=5).astype(np.float64)
     nrec = flags_np.size
-    per = {s: recon_flops(H, s) for s in range(4)}
-    tot_rec = sum(hist[s] * per[s] for s in range(4))
+    per = {s: recon_flops(H, s) for s in range(5)}
+    tot_rec = sum(hist[s] * per[s] for s in range(5))
     nfaces = nrec / ((nd + 2) * 2)
     return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + tot_rec / nfaces, hist / nrec
 
@@ -131,8 +143,8 @@ def executed_fp64_per_face(hist, exact_frac, nd, H):
     filter's own single-precision and integer work is not FP64."""
     nrec = 2 * (nd + 2)
     W = 2 * H
-    algo = sum(hist[s] * recon_flops(H, s) for s in range(4))
-    val = sum(hist[s] * value_flops(H, s) for s in range(4))
+    algo = sum(hist[s] * recon_flops(H, s) for s in range(5))
+    val = sum(hist[s] * value_flops(H, s) for s in range(5))
     per_rec = (W - 1) + (1.0 - exact_frac) * val + exact_frac * algo
     return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + nrec * per_rec
 
@@ -490,6 +502,77 @@ def run_noh(args, dev, stream, n=64, scheme=10, t_end=0.6):
             "pre_shock_cell_scatter_p99": float(np.percentile(np.abs(rho[cell_pre] - exc) / exc, 99))}
 
 
+def selection_mix(hist, scheme):
+    mix = {"fallback": hist[0], "S3": hist[1], "S4": hist[2]}
+    for L in range(5, scheme // 2 + 1):
+        mix["S%d" % L] = hist[L - 2]
+    return mix
+
+
+def run_scheme_leg(args, dev, stream, scheme, n=256, steps=3):
+    """The same 256^3 workload with another scheme width (the twelve-point
+    TENO12-AA): time per step, rate and the face kernel's FP64 roofline
+    fraction (executed flops per face / live average launch time)."""
+    import torch
+
+    import paper_2109_14340_gb300 as T
+    import workloads
+    case = workloads.tgv_3d(n, seed=3001, scheme=scheme)
+    p = T.teno_params_init(ndim=3, n=[n, n, n], dx=case["dx"], scheme=scheme,
+                           bc_lo=[0, 0, 0], bc_hi=[0, 0, 0])
+    solver = T.Solver(p, dev)
+    U = torch.from_numpy(case["U"]).to(dev)
+
+    def step():
+        solver.cfl_dt(U)
+        solver.step(U)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    _, flags = solver.rhs(U, flags=True)
+    fl_np = flags.cpu().numpy()[:flags.numel() // 12 * 10]
+    fpf, hist = flops_per_face_from_flags(fl_np, 3, scheme // 2)
+    del flags, fl_np
+    clocks = ClockSampler(dev.index)
+    T.teno_profile_enable(True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    face_ms, face_launches, face_faces, face_exact = T.teno_profile_read()
+    T.teno_profile_enable(False)
+    clk = clocks.stop()
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    avg_launch_s = face_ms * 1e-3 / max(face_launches, 1)
+    faces_per_launch = face_faces / max(face_launches, 1)
+    exact_frac = face_exact / max(face_faces * 2 * 5, 1)
+    fpf_exec = executed_fp64_per_face(hist, exact_frac, 3, scheme // 2)
+    achieved = fpf_exec * faces_per_launch / avg_launch_s / 1e12
+    method_equiv = fpf * faces_per_launch / avg_launch_s / 1e12
+    traffic_pf = read_traffic_per_face(scheme)
+    return {
+        "workload": "the same 256^3 Taylor-Green + k^-5/3 field with TENO%d-AA, LLF, CFL 0.4"
+                    % scheme,
+        "steps": steps, "ms_per_step": ms / steps, "value": n ** 3 / (ms / steps * 1e-3),
+        "unit": UNIT, "nonphysical": solver.status(), "clocks": clk,
+        "roofline": {"bound": "alu", "kernel": "face_kernel (x/y/z face sweeps)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "fp64_flops_per_face": fpf_exec,
+                     "exact_path_fraction": exact_frac,
+                     "method_equivalent": {"achieved": method_equiv, "frac": method_equiv / peak},
+                     "avg_launch_ms": avg_launch_s * 1e3,
+                     "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
+                     "face_kernel_share": face_ms / ms if ms > 0 else None,
+                     "selection_mix": selection_mix(hist, scheme)},
+    }
+
+
 def read_traffic_per_face(scheme):
     """Measured DRAM bytes per face of the face sweep, from the committed ncu
     summary (a line 'traffic_bytes_per_face[TENO<s>]: <value>')."""
@@ -648,6 +731,9 @@ def run_ours(args, rank, world, local_rank):
     noh = None
     if not args.no_noh:
         noh = run_noh(args, dev, stream)
+    teno12 = None
+    if not args.no_teno12 and scheme != 12:
+        teno12 = run_scheme_leg(args, dev, stream, 12, n=n)
 
     if rank != 0:
         if dist is not None:
@@ -688,7 +774,7 @@ def run_ours(args, rank, world, local_rank):
             "faces_per_launch": faces_per_launch,
             "avg_launch_ms": avg_launch_s * 1e3,
             "face_kernel_share": face_ms / ms if ms > 0 else None,
-            "selection_mix": {"fallback": hist[0], "S3": hist[1], "S4": hist[2], "S5": hist[3]}},
+            "selection_mix": selection_mix(hist, scheme)},
         "roofline_hbm": {
             "bound": "hbm", "achieved": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9,
             "peak": 6782.1, "unit": "GB/s",
@@ -706,6 +792,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "adjoint": adjoint,
         "noh": noh,
+        "teno12": teno12,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -68,7 +68,14 @@ extern "C" {
 
 typedef struct teno_params {
     int32_t ndim;          /* 1, 2 or 3                                         */
-    int32_t scheme;        /* 8 (TENO8-AA, Sec. 4.3) or 10 (TENO10-AA, Sec. 4.2) */
+    int32_t scheme;        /* 8 (TENO8-AA, Sec. 4.3), 10 (TENO10-AA, Sec. 4.2)
+                              or 12 (TENO12-AA: the next member of the family
+                              of Sec. 3.1, its twelve-point candidate S6 built
+                              by the recipe of Sec. 4.1 with the parameters
+                              that give back the printed S3-S5: nu = 7,
+                              tenth-order constraint, 11th-difference part
+                              1/200 on cell i; beta_{6,12} from Eq.
+                              measureTENO)                                    */
     int32_t flux_split;    /* TENO_SPLIT_LLF or TENO_SPLIT_RUSANOV              */
     int32_t limiter;       /* 1: positivity-preserving flux limiter (Sec. 5.3)  */
     int64_t n[3];          /* interior cells per axis, x fastest; 1 if unused;
@@ -113,8 +120,10 @@ int teno_workspace_bytes(const teno_params *p, size_t *bytes);
  * the + then - split flux, one byte: bits 0-1 selected large stencil S_L as
  * L - 2 (1: S3, 2: S4, 3: S5) or 0 for the small-stencil fallback of Eq.
  * renormalize; bits 2-4 the cut-offs delta_0..delta_2 of Eq. cutoff in the
- * fallback (else 0); bits 5-7 the C_T exponent [beta] of Eq. CT_definition
- * minus 7 (mod 8).  Part 2, for each direction in turn, for each face, one
+ * fallback (else 0); S6 of the twelve-point scheme as bits 0-4 all zero (a
+ * fallback always keeps at least one small stencil, so it never writes that
+ * pattern); bits 5-7 the C_T exponent [beta] of Eq. CT_definition minus 7
+ * (mod 8).  Part 2, for each direction in turn, for each face, one
  * little-endian 16-bit word: the stencil cells (0 .. 2H-1, from cell i-H+1)
  * where the splitting speeds are maximal (first maximum), 4 bits each for
  * |u_d - c|, |u_d|, |u_d + c| and |u_d| + c. */
@@ -172,7 +181,7 @@ typedef struct teno_batch_problem {
                               (rho, rho*u, E); offsets 16-byte aligned, state
                               blocks must not overlap                          */
     double dx;             /* spacing (> 0)                                     */
-    int32_t scheme;        /* 8 or 10                                           */
+    int32_t scheme;        /* 8 or 10 (12 is rejected in batched mode)          */
     int32_t limiter;       /* 0 or 1 (positivity-preserving limiter, Sec. 5.3) */
     int32_t bc_lo, bc_hi;  /* TENO_BC_* at the two ends, not TENO_BC_DIRICHLET  */
 } teno_batch_problem;

@@ -1,10 +1,23 @@
 """Write teno_coeffs.cuh: the smoothness-indicator quadratic forms of the
 eight/ten-point TENO-AA schemes (arXiv 2109.14340, Sec. 4.2, Eq. TENO10_AA)
 as doubles, each the round-to-nearest of the printed integer over the printed
-denominator (Python's int / int division is correctly rounded).
+denominator (Python's int / int division is correctly rounded); and the
+twelve-point candidate S6 of TENO12-AA, which the paper names (Sec. 3.1) but
+does not print, derived here:
+* beta_{6,12} from Eq. measureTENO (exact rationals: the degree-11
+  polynomial with the stencil's cell averages, by inverting the cell-average
+  moment matrix), stored like the printed forms;
+* its linear scheme by the recipe of Sec. 4.1: a central part minimising
+  Eq. weighted-error_integral under the accuracy-order constraint (integrals
+  in closed form, 60-digit arithmetic) plus a multiple of the 11th
+  undivided difference, with the parameters that give back the printed
+  S3, S4, S5 (nu = 6, 7, 7; constraints 4, 6, 8; coefficient 1/80, 1/200,
+  1/200 of the difference part on cell i): nu = 7, constraint 10, 1/200.
+  Generation checks that the same routine reproduces the printed schemes.
 
 Layout: upper triangle in ascending stencil offset, Q<w>[r][c] for r <= c,
-offset = index + lo (lo = -2, -3, -4 for widths 6, 8, 10); zeros below.
+offset = index + lo (lo = -2, -3, -4, -5 for widths 6, 8, 10, 12); zeros
+below.  Needs mpmath (generation only; the output is committed).
 Run:  python gen_coeffs.py > teno_coeffs.cuh
 """
 
@@ -65,6 +78,128 @@ W10 = (8002967132160000, -4, [
     (-2, -4, 1159763060479463988),
     (-3, -3, 1348293007163766699), (-3, -4, -308382340247963892),
     (-4, -4, 18029727887840089)])
+
+
+# Printed large-stencil schemes (Sec. 4.1, Eqs. 6-, 8-, 10-point), used here
+# only to check the S6 recipe.
+PRINTED_LIN = {
+    3: [0.02852274270130377, -0.1714015614372447, 0.650378818735941,
+        0.6253788187359414, -0.1589015614372448, 0.02602274270130375],
+    4: [-0.006866688980568011, 0.05128582585522106, -0.1968478198727312,
+        0.6552858258552222, 0.6452858258552218, -0.1908478198727314,
+        0.04928582585522098, -0.006580974694853729],
+    5: [0.001911786299492748, -0.0170332977472532, 0.07339445614860979,
+        -0.221228429084247, 0.6657332621611695, 0.6557332621611695,
+        -0.2145617624175796, 0.07053731329146805, -0.01631901203296621,
+        0.001832421220128962],
+}
+
+
+def indicator_spec(lo, w):
+    """(den, lo, terms) of Eq. measureTENO on cells lo .. lo+w-1: the
+    polynomial p of degree w-1 whose averages over cells [j-1/2, j+1/2] are
+    the stencil values, beta = sum_{m=1}^{w-1} int_{-1/2}^{1/2} (p^(m))^2 dx;
+    terms (a, b, integer) as in the printed forms (off-diagonal coefficient
+    of f_a f_b in full), one common denominator."""
+    from fractions import Fraction as Fr
+    from math import factorial, lcm
+    offs = list(range(lo, lo + w))
+    # moment matrix A[j][l] = average of x^l over cell j, inverted exactly
+    A = [[(Fr(2 * j + 1, 2) ** (l + 1) - Fr(2 * j - 1, 2) ** (l + 1)) / (l + 1)
+          for l in range(w)] + [Fr(int(k == i)) for k in range(w)] for i, j in enumerate(offs)]
+    for c in range(w):
+        piv = next(r for r in range(c, w) if A[r][c] != 0)
+        A[c], A[piv] = A[piv], A[c]
+        A[c] = [x / A[c][c] for x in A[c]]
+        for r in range(w):
+            if r != c and A[r][c] != 0:
+                A[r] = [x - A[r][c] * y for x, y in zip(A[r], A[c])]
+    Minv = [row[w:] for row in A]          # monomial coefficients = Minv f
+    # Gram matrix of the derivatives in the monomial basis
+    def mono_int(k):
+        return Fr(0) if k % 2 else Fr(2, (k + 1) * 2 ** (k + 1))
+    G = [[Fr(0)] * w for _ in range(w)]
+    for m in range(1, w):
+        for l1 in range(m, w):
+            for l2 in range(m, w):
+                G[l1][l2] += (Fr(factorial(l1), factorial(l1 - m)) * Fr(factorial(l2), factorial(l2 - m))
+                              * mono_int(l1 + l2 - 2 * m))
+    Q = [[sum(Minv[l1][a] * G[l1][l2] * Minv[l2][b] for l1 in range(w) for l2 in range(w))
+          for b in range(w)] for a in range(w)]
+    coef = {}
+    for ia in range(w):
+        for ib in range(ia, w):
+            coef[(offs[ia], offs[ib])] = Q[ia][ia] if ia == ib else Q[ia][ib] + Q[ib][ia]
+    den = 1
+    for c in coef.values():
+        den = lcm(den, c.denominator)
+    return (den, lo, [(a, b, int(c * den)) for (a, b), c in coef.items()])
+
+
+def optimised_scheme(r, nu, order, inner):
+    """Face coefficients on offsets -r+1 .. r (Sec. 4.1): central part
+    sum_m a_m sin(m xi) minimising int_0^pi e^(nu (pi - xi)) (sum_m a_m
+    sin(m xi) - xi)^2 dxi with sum_m a_m m = 1 and sum_m a_m m^(2k+1) = 0 for
+    k = 1 .. order/2 - 1; plus inner / C(2r-1, r-1) times the (2r-1)-th
+    difference (-1)^j C(2r-1, j+r-1).  The integrals in closed form with
+    t = pi - xi:  J0(z) = int_0^pi e^(zt) dt, J1(z) = int_0^pi t e^(zt) dt,
+    z = nu - i m."""
+    import mpmath as mp
+    from fractions import Fraction as Fr
+    from math import comb
+    mp.mp.dps = 60
+    nu = mp.mpf(nu)
+    pi = mp.pi
+
+    def J0(z):
+        return (mp.exp(z * pi) - 1) / z
+
+    def J1(z):
+        return mp.exp(z * pi) * (pi / z - 1 / z ** 2) + 1 / z ** 2
+
+    def Ck(k):                              # int e^(nu(pi-xi)) cos(k xi)
+        return mp.re((-1) ** k * J0(mp.mpc(nu, -k))) if k else mp.re(J0(mp.mpc(nu, 0)))
+
+    K = order // 2
+    n = r + K
+    A = mp.matrix(n, n)
+    rhs = mp.matrix(n, 1)
+    for i in range(1, r + 1):
+        rhs[i - 1] = mp.im((-1) ** i * (pi * J0(mp.mpc(nu, -i)) - J1(mp.mpc(nu, -i))))
+        for j in range(1, r + 1):
+            A[i - 1, j - 1] = (Ck(abs(i - j)) - Ck(i + j)) / 2
+        for k in range(K):
+            A[i - 1, r + k] = A[r + k, i - 1] = mp.mpf(i) ** (2 * k + 1)
+    rhs[r] = 1
+    sol = mp.lu_solve(A, rhs)
+    a = [sol[m] for m in range(r)]
+    inner = Fr(inner)
+    unit = mp.mpf(inner.numerator) / (inner.denominator * comb(2 * r - 1, r - 1))
+    out = []
+    for j in range(-r + 1, r + 1):
+        pair = j if j >= 1 else 1 - j       # offsets j and 1-j share the central part
+        central = sum(a[m - 1] for m in range(pair, r + 1)) / 2
+        out.append(float(central + (-1) ** (j % 2) * comb(2 * r - 1, j + r - 1) * unit))
+    return out
+
+
+def s6_scheme():
+    """S6 (offsets -5..6) after checking the recipe on the printed S3-S5 (to
+    their own rounding, 2e-15)."""
+    for L, nu, order, inner in ((3, 6, 4, "1/80"), (4, 7, 6, "1/200"), (5, 7, 8, "1/200")):
+        got = optimised_scheme(L, nu, order, inner)
+        assert max(abs(x - y) for x, y in zip(got, PRINTED_LIN[L])) <= 2e-15, L
+    return optimised_scheme(6, 7, 10, "1/200")
+
+
+def check_printed_indicators():
+    """The indicator routine reproduces the printed forms exactly."""
+    for spec in (W6, W8, W10):
+        den, lo, terms = spec
+        dd, _, tt = indicator_spec(lo, -2 * lo + 2)
+        mine = {(min(a, b), max(a, b)): c for a, b, c in tt}
+        for a, b, c in terms:
+            assert c * dd == mine[(min(a, b), max(a, b))] * den, (lo, a, b)
 
 
 def table(spec):
@@ -213,11 +348,14 @@ def fallback_table():
 
 def emit():
     import numpy as np
+    check_printed_indicators()
+    W12 = indicator_spec(-5, 12)
+    lin6 = s6_scheme()
     out = ["// Generated by gen_coeffs.py from the integers of Eq. TENO10_AA",
-           "// (arXiv 2109.14340, Sec. 4.2); do not edit.",
+           "// (arXiv 2109.14340, Sec. 4.2) and the derived twelve-point S6; do not edit.",
            "#pragma once", ""]
     norms = {}
-    for name, spec in (("TENO_Q6", W6), ("TENO_Q8", W8), ("TENO_Q10", W10)):
+    for name, spec in (("TENO_Q6", W6), ("TENO_Q8", W8), ("TENO_Q10", W10), ("TENO_Q12", W12)):
         w, M = table(spec)
         out.append("static __constant__ double %s[%d][%d] = {" % (name, w, w))
         for r in range(w):
@@ -225,6 +363,12 @@ def emit():
         out.append("};")
         out.append("")
         norms[w] = sym_norms(M, spec[1], w)
+    out.append("// Linear scheme of the twelve-point candidate S6 at face i+1/2, offsets")
+    out.append("// -5..6 (Sec. 4.1 recipe with nu = 7, accuracy constraint 10, 11th-")
+    out.append("// difference part 1/200 on cell i).")
+    out.append("static __constant__ double TENO_LIN6[12] = {")
+    out.append("    " + ", ".join(float.hex(x) for x in lin6) + "};")
+    out.append("")
     out.append("static __constant__ double TENO_DK[3] = {%s};" % ", ".join(DK))
     out.append("// Renormalised fallback weights w_k = d_k delta_k / sum_j d_j delta_j (double")
     out.append("// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index.")
@@ -244,6 +388,7 @@ def emit():
     out += sos_tables("TENO_SOS6", W6, norms[6][1])
     out += sos_tables("TENO_SOS8", W8, norms[8][1])
     out += sos_tables("TENO_SOS10", W10, norms[10][1])
+    out += sos_tables("TENO_SOS12", W12, norms[12][1])
     return "\n".join(out)
 
 

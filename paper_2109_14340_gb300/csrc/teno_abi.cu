@@ -14,6 +14,7 @@ namespace teno {
 // Explicit instantiations live in teno_face8.cu / teno_face10.cu.
 cudaError_t launch_face8(int nd, int d, const FaceArgs &a, cudaStream_t s);
 cudaError_t launch_face10(int nd, int d, const FaceArgs &a, cudaStream_t s);
+cudaError_t launch_face12(int nd, int d, const FaceArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Small kernels
@@ -224,7 +225,7 @@ static int validate(const teno_params *p)
 {
     if (!p) return TENO_EINVAL;
     if (p->ndim < 1 || p->ndim > 3) return TENO_EINVAL;
-    if (p->scheme != 8 && p->scheme != 10) return TENO_EINVAL;
+    if (p->scheme != 8 && p->scheme != 10 && p->scheme != 12) return TENO_EINVAL;
     if (p->flux_split != TENO_SPLIT_LLF && p->flux_split != TENO_SPLIT_RUSANOV) return TENO_EINVAL;
     if (p->limiter != 0 && p->limiter != 1) return TENO_EINVAL;
     if (p->q != 7 || p->reserved != 0) return TENO_EINVAL;
@@ -388,7 +389,8 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
             g_prof.nf[slot] = a.nfaces - (a.skip_last ? a.ncell / p->n[d] : 0);   // faces computed
             CUDA_TRY(profile_mark(0, slot, s));
         }
-        cudaError_t e = (p->scheme == 8) ? launch_face8(nd, d, a, s) : launch_face10(nd, d, a, s);
+        cudaError_t e = (p->scheme == 8) ? launch_face8(nd, d, a, s)
+                      : (p->scheme == 10 ? launch_face10(nd, d, a, s) : launch_face12(nd, d, a, s));
         if (e != cudaSuccess) return TENO_ECUDA;
         if (slot >= 0) CUDA_TRY(profile_mark(1, slot, s));
         if (fl) fl += (size_t)face_grid(p, d) * nc * 2;
@@ -600,7 +602,8 @@ int teno_advance_host(const teno_params *p, double *U_host, double *U_dev, int n
 int teno_reconstruct(const teno_params *p, const double *v, int64_t count, double *out,
                      uint8_t *flags, void *stream)
 {
-    if (!p || (p->scheme != 8 && p->scheme != 10) || count < 0 || !v || !out) return TENO_EINVAL;
+    if (!p || (p->scheme != 8 && p->scheme != 10 && p->scheme != 12) || count < 0 || !v || !out)
+        return TENO_EINVAL;
     if (!(p->ct_cr > 0.0) || !(p->eps_beta >= 0.0) || !(p->eps_eta > 0.0)) return TENO_EINVAL;
     if (count == 0) return TENO_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -608,7 +611,8 @@ int teno_reconstruct(const teno_params *p, const double *v, int64_t count, doubl
     const FastK FK = fastk_of(p);
     const int blk = 128, grd = grid_for(count, blk);
     if (p->scheme == 8) recon_kernel<4><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
-    else recon_kernel<5><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
+    else if (p->scheme == 10) recon_kernel<5><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
+    else recon_kernel<6><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
     CUDA_TRY(cudaGetLastError());
     return TENO_OK;
 }

@@ -814,8 +814,9 @@ int rhs_vjp_impl(const teno_params *p, const double *U, const double *lam, const
         a.bc_hi = p->bc_hi[d];
         a.inv_dx = 1.0 / p->dx[d];
         a.K = consts_adj(p);
-        cudaError_t e = (p->scheme == 8) ? launch_adj<4>(p->ndim, d, a, mu, d > 0, s)
-                                         : launch_adj<5>(p->ndim, d, a, mu, d > 0, s);
+        cudaError_t e = (p->scheme == 8)    ? launch_adj<4>(p->ndim, d, a, mu, d > 0, s)
+                        : (p->scheme == 10) ? launch_adj<5>(p->ndim, d, a, mu, d > 0, s)
+                                            : launch_adj<6>(p->ndim, d, a, mu, d > 0, s);
         if (e != cudaSuccess) return TENO_ECUDA;
         fl += (size_t)faces_of(p, d) * nc * 2;
     }

@@ -364,7 +364,11 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
     for (int p = 0; p < nprob; p++) {
         const teno_batch_problem &q = probs[p];
         teno_params pp;
-        if (problem_params(b, p, &pp) != TENO_OK || q.offset < 0 || (q.offset & 1)) {
+        // batched problems use the eight- and ten-point schemes only (the
+        // persistent kernel holds both instantiations; a third would raise
+        // its registers and shared memory for every problem)
+        if (problem_params(b, p, &pp) != TENO_OK || q.offset < 0 || (q.offset & 1) ||
+            (q.scheme != 8 && q.scheme != 10)) {
             delete b;
             return TENO_EINVAL;
         }

@@ -24,7 +24,8 @@ struct Status {
 static_assert(sizeof(Status) == 256, "status block is 256 bytes");
 
 // Optimal linear schemes on the large stencils (Sec. 4.1, Eqs. 6-, 8-,
-// 10-point), ascending offsets -2..3, -3..4, -4..5.
+// 10-point), ascending offsets -2..3, -3..4, -4..5.  The twelve-point S6
+// (offsets -5..6, TENO_LIN6) is generated with the indicator tables.
 static __constant__ double TENO_LIN3[6] = {
     0.02852274270130377, -0.1714015614372447, 0.650378818735941,
     0.6253788187359414, -0.1589015614372448, 0.02602274270130375};
@@ -65,14 +66,38 @@ __device__ __forceinline__ double scale_sep(double beta, double eps)
     return 1.0 / x7;
 }
 
+// Decision-byte code of the large stencil S_L: L - 2 in bits 0-1 for S3..S5;
+// S6 (twelve-point scheme) as bits 0-4 all zero -- a fallback always keeps at
+// least one small stencil (the three chi_k sum to one), so its cut-off bits
+// are never all zero.
+__host__ __device__ constexpr int large_code(int L) { return L == 6 ? 0 : L - 2; }
+
+// Table entries of the indicator form / linear scheme of S_L.
+template <int L>
+__device__ __forceinline__ double qcoef(int r, int c)
+{
+    if constexpr (L == 3) return TENO_Q6[r][c];
+    else if constexpr (L == 4) return TENO_Q8[r][c];
+    else if constexpr (L == 5) return TENO_Q10[r][c];
+    else return TENO_Q12[r][c];
+}
+template <int L>
+__device__ __forceinline__ double lcoef(int r)
+{
+    if constexpr (L == 3) return TENO_LIN3[r];
+    else if constexpr (L == 4) return TENO_LIN4[r];
+    else if constexpr (L == 5) return TENO_LIN5[r];
+    else return TENO_LIN6[r];
+}
+
 // Smoothness indicator of the large stencil S_L (Eq. TENO10_AA quadratic
-// forms) on data shifted by the cell-i value, sh[m + H - 1] = v_m - v_0 for
-// the whole 2H stencil; terms of the zero shifted value are skipped (they add
-// exact zeros).
+// forms; beta_{6,12} derived from Eq. measureTENO) on data shifted by the
+// cell-i value, sh[m + H - 1] = v_m - v_0 for the whole 2H stencil; terms of
+// the zero shifted value are skipped (they add exact zeros).
 template <int H, int L>
 __device__ __forceinline__ double beta_large_s(const double (&sh)[2 * H])
 {
-    constexpr int lo = (L == 3) ? -2 : (L == 4 ? -3 : -4);
+    constexpr int lo = 1 - L;                     // S_L covers offsets 1-L .. L
     constexpr int w = 2 * L;
     double s[w];
 #pragma unroll
@@ -81,13 +106,11 @@ __device__ __forceinline__ double beta_large_s(const double (&sh)[2 * H])
 #pragma unroll
     for (int r = 0; r < w; r++) {
         if (r + lo == 0) continue;                // s == 0: contributes nothing
-        double coef_rr = (L == 3) ? TENO_Q6[r][r] : (L == 4 ? TENO_Q8[r][r] : TENO_Q10[r][r]);
-        double inner = coef_rr * s[r];
+        double inner = qcoef<L>(r, r) * s[r];
 #pragma unroll
         for (int c = r + 1; c < w; c++) {
             if (c + lo == 0) continue;
-            double cf = (L == 3) ? TENO_Q6[r][c] : (L == 4 ? TENO_Q8[r][c] : TENO_Q10[r][c]);
-            inner = fma(cf, s[c], inner);
+            inner = fma(qcoef<L>(r, c), s[c], inner);
         }
         acc = (r == 0) ? s[r] * inner : fma(s[r], inner, acc);
     }
@@ -106,15 +129,11 @@ __device__ __forceinline__ double beta_large(const double (&v)[2 * H])
 template <int H, int L>
 __device__ __forceinline__ double flux_large(const double (&v)[2 * H])
 {
-    constexpr int lo = (L == 3) ? -2 : (L == 4 ? -3 : -4);
+    constexpr int lo = 1 - L;
     constexpr int w = 2 * L;
-    double c0 = (L == 3) ? TENO_LIN3[0] : (L == 4 ? TENO_LIN4[0] : TENO_LIN5[0]);
-    double acc = c0 * v[lo + H - 1];
+    double acc = lcoef<L>(0) * v[lo + H - 1];
 #pragma unroll
-    for (int r = 1; r < w; r++) {
-        double cr = (L == 3) ? TENO_LIN3[r] : (L == 4 ? TENO_LIN4[r] : TENO_LIN5[r]);
-        acc = fma(cr, v[lo + r + H - 1], acc);
-    }
+    for (int r = 1; r < w; r++) acc = fma(lcoef<L>(r), v[lo + r + H - 1], acc);
     return acc;
 }
 
@@ -168,7 +187,7 @@ __device__ __forceinline__ double fallback_value(const double (&v)[2 * H], int m
 
 // One reconstruction; flag: bits 0-1 selected large stencil (L-2) or 0 for the
 // small-stencil fallback, bits 2-4 deltas of S0..S2 (fallback), bits 5-7 C_T
-// exponent minus 7.
+// exponent minus 7; S6 as bits 0-4 zero (large_code).
 template <int H>
 __device__ __forceinline__ double teno_recon(const double (&v)[2 * H], const Consts &K,
                                              uint8_t &flag)
@@ -193,7 +212,12 @@ __device__ __forceinline__ double teno_recon(const double (&v)[2 * H], const Con
     double g012 = (g0 + g1) + g2;
 
     // Targeted ENO-like selection (Sec. 3.3), largest group first.
-    if (H == 5) {
+    if constexpr (H == 6) {
+        double g6 = scale_sep(beta_large<H, 6>(v), K.eps_beta);
+        double chi = g6 / (g012 + g6);
+        if (!(chi < CT)) { flag = fct; return flux_large<H, 6>(v); }
+    }
+    if constexpr (H >= 5) {
         double g5 = scale_sep(beta_large<H, 5>(v), K.eps_beta);
         double chi = g5 / (g012 + g5);
         if (!(chi < CT)) { flag = (uint8_t)(3 | fct); return flux_large<H, 5>(v); }
@@ -226,8 +250,15 @@ template <int H>
 __device__ __forceinline__ double decided_value(const double (&v)[2 * H], uint8_t flag)
 {
     const int sel = flag & 3;
-    if (sel == H - 2) return flux_large<H, H>(v);
-    if (H == 5 && sel == 2) return flux_large<H, 4>(v);
+    if constexpr (H == 6) {
+        if ((flag & 31) == 0) return flux_large<H, 6>(v);
+        if (sel == 3) return flux_large<H, 5>(v);
+    } else {
+        if (sel == H - 2) return flux_large<H, H>(v);
+    }
+    if constexpr (H >= 5) {
+        if (sel == 2) return flux_large<H, 4>(v);
+    }
     if (sel == 1) return flux_large<H, 3>(v);
     return fallback_value<H>(v, (flag >> 2) & 7);
 }
@@ -240,6 +271,9 @@ __device__ __forceinline__ double frozen_coef(uint8_t flag, int m)
 {
     const int sel = flag & 3;
     const int off = m - H + 1;
+    if constexpr (H == 6) {
+        if ((flag & 31) == 0) return (off >= -5 && off <= 6) ? TENO_LIN6[off + 5] : 0.0;
+    }
     if (sel == 3) return (off >= -4 && off <= 5) ? TENO_LIN5[off + 4] : 0.0;
     if (sel == 2) return (off >= -3 && off <= 4) ? TENO_LIN4[off + 3] : 0.0;
     if (sel == 1) return (off >= -2 && off <= 3) ? TENO_LIN3[off + 2] : 0.0;

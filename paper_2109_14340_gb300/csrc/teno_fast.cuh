@@ -166,6 +166,31 @@ __device__ __forceinline__ void small_beta(float a, float ea, float b, float eb,
 //   |beta - beta~| <= E = (n+3) 2^-24 beta~ + TAU2 sum_i DC_i |y_i| + K0
 // (TAU2, DC, K0 as generated with the tables).  The final factors cover the
 // FP32 rounding of the bounds themselves; lo may be negative.
+template <int L>
+__device__ __forceinline__ float sos_l(int m, int i)
+{
+    if constexpr (L == 3) return TENO_SOS6_L[m][i];
+    else if constexpr (L == 4) return TENO_SOS8_L[m][i];
+    else if constexpr (L == 5) return TENO_SOS10_L[m][i];
+    else return TENO_SOS12_L[m][i];
+}
+template <int L>
+__device__ __forceinline__ float sos_d(int i)
+{
+    if constexpr (L == 3) return TENO_SOS6_D[i];
+    else if constexpr (L == 4) return TENO_SOS8_D[i];
+    else if constexpr (L == 5) return TENO_SOS10_D[i];
+    else return TENO_SOS12_D[i];
+}
+template <int L>
+__device__ __forceinline__ float sos_dc(int i)
+{
+    if constexpr (L == 3) return TENO_SOS6_DC[i];
+    else if constexpr (L == 4) return TENO_SOS8_DC[i];
+    else if constexpr (L == 5) return TENO_SOS10_DC[i];
+    else return TENO_SOS12_DC[i];
+}
+
 template <int H, int L>
 __device__ __forceinline__ void beta_large_bounds(const float (&f)[2 * H], float &lo, float &hi)
 {
@@ -178,16 +203,13 @@ __device__ __forceinline__ void beta_large_bounds(const float (&f)[2 * H], float
 #pragma unroll
         for (int m = i + 1; m < n; m++) {
             const int om = m < L ? L - m : L - 1 - m;
-            const float l = (L == 5) ? TENO_SOS10_L[m][i] : (L == 4 ? TENO_SOS8_L[m][i] : TENO_SOS6_L[m][i]);
-            y = fmaf(l, f[om + H - 1], y);
+            y = fmaf(sos_l<L>(m, i), f[om + H - 1], y);
         }
-        const float d = (L == 5) ? TENO_SOS10_D[i] : (L == 4 ? TENO_SOS8_D[i] : TENO_SOS6_D[i]);
-        const float dc = (L == 5) ? TENO_SOS10_DC[i] : (L == 4 ? TENO_SOS8_DC[i] : TENO_SOS6_DC[i]);
-        bt = fmaf(d, y * y, bt);
-        eb = fmaf(dc, fabsf(y), eb);
+        bt = fmaf(sos_d<L>(i), y * y, bt);
+        eb = fmaf(sos_dc<L>(i), fabsf(y), eb);
     }
-    const float tau2 = (L == 5) ? TENO_SOS10_TAU2 : (L == 4 ? TENO_SOS8_TAU2 : TENO_SOS6_TAU2);
-    const float k0 = (L == 5) ? TENO_SOS10_K0 : (L == 4 ? TENO_SOS8_K0 : TENO_SOS6_K0);
+    const float tau2 = (L == 3) ? TENO_SOS6_TAU2 : (L == 4 ? TENO_SOS8_TAU2 : (L == 5 ? TENO_SOS10_TAU2 : TENO_SOS12_TAU2));
+    const float k0 = (L == 3) ? TENO_SOS6_K0 : (L == 4 ? TENO_SOS8_K0 : (L == 5 ? TENO_SOS10_K0 : TENO_SOS12_K0));
     const float E = fmaf(tau2, eb, fmaf(bt, (float)(n + 3) * 5.9604645e-8f, k0));
     hi = (bt + E) * (1.0f + 4.0e-6f);
     lo = fmaf(-E, 1.00001f, bt) * (1.0f - 1.0e-6f);
@@ -250,7 +272,7 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
 #pragma unroll
     for (int j = 0; j < W; j++) all_eq = all_eq && dbits_equal(v[j], v[H - 1]);
     if (all_eq) {
-        flag = (uint8_t)((H - 2) | (((F.nexp_smooth - 7) & 7) << 5));
+        flag = (uint8_t)(large_code(H) | (((F.nexp_smooth - 7) & 7) << 5));
         return true;
     }
     // Common scale: the largest exponent among the shifted values.
@@ -355,7 +377,10 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const int sel = select_large<H, H>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
     if (sel < 0) return false;
     if (sel > 0) {
-        flag = (uint8_t)(sel | fct);
+        if constexpr (H == 6)
+            flag = (uint8_t)((sel == 4 ? 0 : sel) | fct);     // S6: bits 0-4 zero
+        else
+            flag = (uint8_t)(sel | fct);
         return true;
     }
 

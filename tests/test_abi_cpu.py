@@ -58,7 +58,8 @@ def test_workspace_sizing(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(scheme=9), dict(ndim=4), dict(q=2), dict(gamma=1.0), dict(n=[3]),
+    dict(scheme=9), dict(scheme=11), dict(scheme=14), dict(scheme=12, n=[5]),
+    dict(ndim=4), dict(q=2), dict(gamma=1.0), dict(n=[3]),
     dict(bc_lo=[0], bc_hi=[1]), dict(bc_lo=[5], bc_hi=[5]), dict(dx=[0.0]),
     dict(flux_split=2), dict(limiter=2), dict(ct_cr=0.0), dict(n=[64, 2]),
     dict(ndim=3, n=[8, 8, 65536], dx=[0.1] * 3), dict(ndim=2, n=[8, 65536], dx=[0.1] * 2),
@@ -95,7 +96,14 @@ def test_batch_plan_host_logic(lib):
         lib.teno_batch_destroy(h)
 
 
-@pytest.mark.parametrize("bad", ["overlap", "odd_offset", "too_small", "scheme"])
+def test_twelve_point_scheme_accepted(lib):
+    """scheme 12 (TENO12-AA) is valid with n >= 6 on every used axis."""
+    for kw in (dict(ndim=1, n=[6], dx=[0.1]), dict(ndim=3, n=[6, 7, 8], dx=[0.1] * 3)):
+        p = lib.teno_params_init(scheme=12, **kw)
+        assert lib.teno_workspace_bytes(p) > 0
+
+
+@pytest.mark.parametrize("bad", ["overlap", "odd_offset", "too_small", "scheme", "scheme12"])
 def test_batch_plan_rejects(lib, bad):
     common = lib.teno_params_init()
     sizes, schemes, offs = [64, 64], [8, 10], None
@@ -107,6 +115,8 @@ def test_batch_plan_rejects(lib, bad):
         sizes = [64, 4]
     elif bad == "scheme":
         schemes = [8, 9]
+    elif bad == "scheme12":            # batched mode runs the 8/10-point schemes only
+        schemes = [8, 12]
     with pytest.raises(lib.TenoError) as e:
         lib.teno_batch_create(common, _probs(lib, sizes, schemes, offs))
     assert e.value.code == lib.TENO_EINVAL

@@ -56,6 +56,9 @@ CASES = [
     ("3d-periodic-s10-llf", 3, [12, 11, 10], 10, [0, 0, 0], [0, 0, 0], 0),
     ("2d-noslip-s8-llf", 2, [22, 20], 8, [3, 0], [2, 0], 0),
     ("3d-noslip-s10-rus", 3, [12, 11, 10], 10, [3, 1, 0], [1, 3, 0], 1),
+    ("1d-periodic-s12-llf", 1, [48], 12, [0], [0], 0),
+    ("2d-slip-s12-rus", 2, [24, 22], 12, [2, 1], [2, 1], 1),
+    ("3d-noslip-s12-rus", 3, [12, 11, 10], 12, [3, 1, 0], [1, 3, 0], 1),
 ]
 
 
@@ -82,7 +85,7 @@ def test_rhs_vjp_dot_product(name, nd, n, scheme, lo, hi, split):
     T.teno_rhs_vjp(p, U, lam, mu, None, aws)
     _, fl0 = gpu_rhs_flags(p, U)
     checked = 0
-    for seed in (31, 32, 33, 34, 35):
+    for seed in (31, 32, 33, 34, 35, 36, 37, 38):
         v = torch.from_numpy(direction(nd, n, seed)).to(DEV)
         for h in (1e-6, 1e-7):
             Lp, flp = gpu_rhs_flags(p, U + h * v)
@@ -99,7 +102,7 @@ def test_rhs_vjp_dot_product(name, nd, n, scheme, lo, hi, split):
     assert checked >= 2
 
 
-@pytest.mark.parametrize("scheme,split", [(8, 0), (10, 1)])
+@pytest.mark.parametrize("scheme,split", [(8, 0), (10, 1), (12, 0)])
 def test_rhs_vjp_matches_oracle_reference(scheme, split):
     """Full J^T lam of a 1D periodic problem, assembled from central
     differences of the CPU oracle, one conserved variable of one cell at a
@@ -252,9 +255,10 @@ def _setup(nx, ny, nsteps, every):
     return c, p, dt, U0, rho_t, U0g.grad
 
 
-def test_frozen_rhs_equals_deciding_rhs():
+@pytest.mark.parametrize("scheme", [10, 12])
+def test_frozen_rhs_equals_deciding_rhs(scheme):
     nd, n = 2, [30, 26]
-    p = T.teno_params_init(ndim=nd, n=n, dx=[1.0 / k for k in n], scheme=10, bc_lo=[1, 0],
+    p = T.teno_params_init(ndim=nd, n=n, dx=[1.0 / k for k in n], scheme=scheme, bc_lo=[1, 0],
                            bc_hi=[1, 0])
     U = torch.from_numpy(smooth_state(nd, n, 71)).to(DEV)
     s = T.Solver(p)

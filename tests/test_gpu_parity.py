@@ -67,7 +67,7 @@ def gpu_rhs(p, U, dt_lim=0.0):
 def _cases():
     g = np.random.Generator(np.random.PCG64(77))
     out = []
-    for scheme in (8, 10):
+    for scheme in (8, 10, 12):
         for bc in (0, 1, 2):
             c = workloads.riemann_1d(137, seed=1001 + bc, scheme=scheme)
             c["bc_lo"] = [bc, 0, 0]
@@ -90,7 +90,7 @@ def _cases():
                                         bc_lo=[1, 2, 0], bc_hi=[2, 1, 0], scheme=10,
                                         gamma=1.4)))
     # no-slip (App. A.2) and Dirichlet (App. A.3) sides
-    for scheme in (8, 10):
+    for scheme in (8, 10, 12):
         out.append(("1d-dirichlet-noslip-s%d" % scheme,
                     workloads.boundary_walls(1, [97], [4], [3], seed=6001, scheme=scheme)))
         out.append(("2d-dirichlet-noslip-s%d" % scheme,
@@ -213,7 +213,7 @@ def test_advance_host_matches_device_path():
     assert torch.equal(Uh, Ud.cpu())
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_full_size_3d_sampled(scheme):
     """256^3 periodic Taylor-Green + k^-5/3 field, the launch configuration
     of the benchmark: the RHS at sampled cells (corners, faces, interior)
@@ -255,7 +255,7 @@ def test_full_size_2d_sampled():
 # edge cases
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_minimum_grid(scheme):
     """n = H cells per axis (the smallest valid grid) in 2D, periodic and
     slip walls."""

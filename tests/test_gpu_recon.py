@@ -76,7 +76,7 @@ def adversarial(scheme):
     H = scheme // 2
     offs = np.arange(-H + 1, H + 1, dtype=float)
     po = oracle.params(1, [16], [1.0], scheme=scheme)
-    key_sel = lambda v: oracle.recon(po, v)[1] & 3
+    key_sel = lambda v: oracle.decode_flag(oracle.recon(po, v)[1])[0]
     key_ct = lambda v: (oracle.recon(po, v)[1] >> 5) & 7
     out = []
     # chi_p = C_T: a step at the largest stencil's edge, C_T = 1e-14 region
@@ -160,7 +160,7 @@ def random_stencils(scheme, n=20000, seed=7):
     return np.array(V)
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_reconstruction_matches_oracle(scheme):
     V = np.concatenate([random_stencils(scheme), adversarial(scheme)])
     ref, rfl = oracle_batch(scheme, V)
@@ -170,14 +170,16 @@ def test_reconstruction_matches_oracle(scheme):
         assert bad.size == 0, (fast, bad[:10], fl[bad[:5]], rfl[bad[:5]])
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_adversarial_families_reach_both_sides(scheme):
     """The bisected families really straddle thresholds (both outcomes)."""
     V = adversarial(scheme)
     _, rfl = oracle_batch(scheme, V)
     assert len(V) > 50
-    assert len(set((rfl & 3).tolist())) >= 2
+    dec = [oracle.decode_flag(int(f)) for f in rfl]
+    sels = {d[0] for d in dec}
+    assert len(sels) >= 2
     assert len(set(((rfl >> 5) & 7).tolist())) >= 5
-    # every selectable large stencil, and fallbacks with different cut-offs
-    assert set(range(1, scheme // 2 - 1)) <= set((rfl & 3).tolist())
-    assert len(set(((rfl >> 2) & 7)[(rfl & 3) == 0].tolist())) >= 3
+    # every large stencil S3 .. S_H, and fallbacks with different cut-offs
+    assert set(range(3, scheme // 2 + 1)) <= sels
+    assert len({d[1] for d in dec if d[0] == 0}) >= 3

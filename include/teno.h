@@ -3,9 +3,11 @@
  *
  * The library evaluates the semi-discrete right-hand side of the compressible
  * Euler equations (arXiv 2109.14340, Sec. 1 Eq. Euler; Sec. 2 Eq.
- * approximateEq) with the eight- or ten-point TENO-AA reconstruction (Sec. 3,
- * Sec. 4) of Roe-averaged characteristic, flux-split fluxes (Sec. 5), and
- * advances it with SSP-RK3 (Sec. 5, Eq. Runge-kutta) under a CFL time step.
+ * approximateEq) with the eight-, ten- or twelve-point TENO-AA reconstruction
+ * (Sec. 3, Sec. 4; the twelve-point candidate S6 built by the recipe of Sec.
+ * 4.1, see teno_params.scheme) of Roe-averaged characteristic, flux-split
+ * fluxes (Sec. 5), and advances it with SSP-RK3 (Sec. 5, Eq. Runge-kutta)
+ * under a CFL time step.
  *
  * Conventions shared by every call:
  *  - State arrays are FP64, structure of arrays, interior cells only:

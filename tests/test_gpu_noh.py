@@ -41,7 +41,7 @@ def set_states(c, st, t):
         st[d].copy_(torch.from_numpy(a))
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_noh_parity_steps(scheme):
     c, st, p = setup(20, scheme)
     S = T.Solver(p)
@@ -64,7 +64,7 @@ def test_noh_parity_steps(scheme):
         t += dt_o
 
 
-@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_noh_analytic_solution(scheme):
     n, t_end = 64, 0.6
     c, st, p = setup(n, scheme)

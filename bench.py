@@ -260,6 +260,13 @@ def whole_job_rate(world: int, cells_per_rank: int, steps: int, seconds: float) 
     return world * cells_per_rank * steps / seconds
 
 
+def workload_desc(n, scheme):
+    """The benchmark workload, the same string on both arms."""
+    return ("3D Euler %d^3 periodic on [0,2pi]^3, Taylor-Green Mach 0.5 + seeded k^-5/3 "
+            "solenoidal field (10%% rms), TENO%d-AA, LLF, CFL 0.4; step = CFL time step + "
+            "SSP-RK3 step" % (n, scheme))
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -291,8 +298,7 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "3D Euler 256^3 periodic, Taylor-Green Mach 0.5 + k^-5/3 "
-                                   "solenoidal field, TENO%d-AA, LLF, CFL 0.4" % scheme,
+            "config": {"workload": workload_desc(n, scheme), "scheme": scheme, "cells": n ** 3,
                        "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
@@ -751,9 +757,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {
-            "workload": "3D Euler 256^3 periodic on [0,2pi]^3, Taylor-Green Mach 0.5 + seeded "
-                        "k^-5/3 solenoidal field (10%% rms), TENO%d-AA, LLF, CFL 0.4; step = "
-                        "device CFL reduction + SSP-RK3 step" % scheme,
+            "workload": workload_desc(n, scheme),
             "scheme": scheme, "cells": cells, "parallelism": "independent problem per GPU",
             "l2": "state 671 MB > 129 MB L2 (no flush needed)"},
         "roofline": {

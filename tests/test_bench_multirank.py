@@ -74,3 +74,19 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_twelve_point_scheme():
+    """The reference arm (the oracle) runs the TENO12-AA workload too, on the
+    same workload description as our arm."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scheme", "12",
+           "--steps", "1", "--warmup", "1", "--size", "24"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["config"]["scheme"] == 12
+    assert d["config"]["workload"] == bench.workload_desc(24, 12)

@@ -9,6 +9,9 @@ code.
 Parity pins live in ``tests/test_oracle_*.py``.  Parity unpinned: the exact
 formula of the positivity-preserving limiter (Sec. 5.3 cites it without stating
 it); only its invariants (positivity, theta = 1 on smooth data) are pinned.
+The twelve-point candidate S6 (``teno12_derive.py``) is not printed; its
+recipe is pinned on the printed S3-S5 and its result on order, optimality and
+the exact indicator derivation.
 """
 from __future__ import annotations
 

@@ -24,7 +24,11 @@
  * recovery, conservation, free stream, positivity, exact Riemann solutions,
  * RK3 stability polynomial).  Parity unpinned: the positivity limiter's exact
  * formula (the paper cites it without stating it); only its invariants are
- * pinned.
+ * pinned.  The twelve-point S6 is not printed: its recipe parameters (nu = 7,
+ * tenth-order constraint, 1/200 of the 11th difference on cell i) are the
+ * ones that reproduce the printed S3-S5, which the tests check, together with
+ * S6's order, its optimality for the weighted error integral and its
+ * indicator's exact derivation.
  */
 #include <math.h>
 #include <stdint.h>

@@ -90,3 +90,21 @@ def test_reference_arm_twelve_point_scheme():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["config"]["scheme"] == 12
     assert d["config"]["workload"] == bench.workload_desc(24, 12)
+
+
+def test_flop_accounting_reads_the_s6_code():
+    """The roofline's FP64 count per face classifies decision bytes the way
+    the kernels write them: S6 of the twelve-point scheme as bits 0-4 zero,
+    S3..S5 as L - 2 in bits 0-1, the fallback as 0 with cut-off bits."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    fl = np.array([0x20, 0xE1, 0x42, 0x63, 0x04, 0x1C, 0x00], np.uint8)
+    assert bench.selection_class(fl, 6).tolist() == [4, 1, 2, 3, 0, 0, 4]
+    assert bench.selection_class(fl, 5).tolist() == [0, 1, 2, 3, 0, 0, 0]
+    # S6: the common part, one indicator of 11 non-zero shifted values
+    # (11 + 121 + 21 flops), its test (8) and its 12-point scheme (23)
+    assert bench.recon_flops(6, 4) == 101 + 153 + 8 + 23
+    assert bench.value_flops(6, 4) == 23
+    # the S5 path of TENO12 first tests S6, then S5
+    assert bench.recon_flops(6, 3) == 101 + 153 + 8 + (9 + 81 + 17) + 8 + 19

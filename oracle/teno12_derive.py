@@ -3,8 +3,8 @@ INFRASTRUCTURE ONLY (part of the oracle).
 
 The paper builds its very-high-order family recursively (Sec. 3.1): the
 three small stencils plus symmetric large stencils of growing width; it
-names TENO12 and wider schemes as members but prints coefficients only up
-to the ten-point stencil S5.  This script derives S6 (offsets -5..6) the
+states that the framework extends to any width but prints coefficients
+only up to the ten-point stencil S5.  This script derives S6 (offsets -5..6) the
 way Sec. 4.1 and Sec. 4.2 describe the printed ones:
 
 * the smoothness indicator beta_{6,12} from Eq. measureTENO, for the

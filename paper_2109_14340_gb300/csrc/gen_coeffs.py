@@ -2,8 +2,8 @@
 eight/ten-point TENO-AA schemes (arXiv 2109.14340, Sec. 4.2, Eq. TENO10_AA)
 as doubles, each the round-to-nearest of the printed integer over the printed
 denominator (Python's int / int division is correctly rounded); and the
-twelve-point candidate S6 of TENO12-AA, which the paper names (Sec. 3.1) but
-does not print, derived here:
+twelve-point candidate S6 of TENO12-AA -- the next member of the family the
+paper builds (Sec. 3.1), which it does not print -- derived here:
 * beta_{6,12} from Eq. measureTENO (exact rationals: the degree-11
   polynomial with the stencil's cell averages, by inverting the cell-average
   moment matrix), stored like the printed forms;

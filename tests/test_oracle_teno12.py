@@ -1,5 +1,5 @@
-"""Pins of the oracle's twelve-point candidate S6 (TENO12-AA), which the paper
-names as the next member of its family (Sec. 3.1) but does not print.
+"""Pins of the oracle's twelve-point candidate S6 (TENO12-AA): the next member
+of the family the paper builds (Sec. 3.1), which it does not print.
 
 The oracle derives S6 with oracle/teno12_derive.py.  These tests pin that
 derivation to what the paper does print and to the mathematics:

@@ -295,7 +295,10 @@ int teno_rk3_step_vjp(const teno_params *p, const double *Un, const double *U1, 
  *   enqueued.  Allocates nothing (no cudaMalloc / cudaFree).
  *   The first call on a device resolves the array's device address (one
  *   cudaGetSymbolAddress with that device current); make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept per device together with
+ *   the id of the context it came from and resolved again when another
+ *   context is current (after cudaDeviceReset, which unloads the array with
+ *   the context), so that first-call rule applies again after a reset.
  *   All calls share the one array and each zeroes its status header: calls
  *   whose work overlaps on the GPU (different streams, or different host
  *   threads without ordering) race on it and must be serialised by the
@@ -321,7 +324,11 @@ int teno_reconstruct(const teno_params *p, const double *v, int64_t count, doubl
  * evaluation whenever the bounds leave the decision open; 0 always evaluates
  * the decisions in FP64.  Results are identical either way (the filter only
  * answers when its answer equals the FP64 one); the switch exists to test
- * and time that.  Not thread-safe with concurrent launches. */
+ * and time that.  The filter's error bounds take the epsilons of Sec. 3.2
+ * and Sec. 3.4 as negligible above 2^-100, which holds for eps_beta and
+ * eps_eta at most 1e-40 (the paper's value): with a larger epsilon every
+ * decision is evaluated in FP64 whatever the switch says.  Not thread-safe
+ * with concurrent launches. */
 int teno_set_decision_filter(int on);
 
 /* Live timing of the dominant kernel (the face-sweep kernel) for roofline

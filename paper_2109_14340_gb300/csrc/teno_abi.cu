@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "teno.h"
 #include "teno_face.cuh"
 
@@ -285,6 +287,12 @@ static FastK fastk_of(const teno_params *p)
     return fastk_make(p->ct_cr, p->ct_alpha1, p->ct_alpha2);
 }
 
+// The filter runs when it is switched on and its bounds hold for p's epsilons.
+static int filter_on(const teno_params *p)
+{
+    return g_fast_filter && fast_filter_valid(p->eps_beta, p->eps_eta) ? 1 : 0;
+}
+
 static double3 inv_dx_of(const teno_params *p)
 {
     return make_double3(1.0 / p->dx[0], 1.0 / p->dx[1], 1.0 / p->dx[2]);
@@ -378,7 +386,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.bcs_lo = p->bc_state_lo[d];
         a.bcs_hi = p->bc_state_hi[d];
         a.lam = &st->lam[d];
-        a.fast = g_fast_filter;
+        a.fast = filter_on(p);
         a.skip_last = (p->bc_lo[d] == TENO_BC_PERIODIC && !fl && !fz) ? 1 : 0;
         a.count_cells = (d == 0);                 // the x sweep counts the stage input's cells
         a.exact_count = g_prof.on ? g_prof.exact : nullptr;
@@ -609,10 +617,11 @@ int teno_reconstruct(const teno_params *p, const double *v, int64_t count, doubl
     cudaStream_t s = (cudaStream_t)stream;
     const Consts K = consts_of(p);
     const FastK FK = fastk_of(p);
+    const int fast = filter_on(p);
     const int blk = 128, grd = grid_for(count, blk);
-    if (p->scheme == 8) recon_kernel<4><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
-    else if (p->scheme == 10) recon_kernel<5><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
-    else recon_kernel<6><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, g_fast_filter);
+    if (p->scheme == 8) recon_kernel<4><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, fast);
+    else if (p->scheme == 10) recon_kernel<5><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, fast);
+    else recon_kernel<6><<<grd, blk, 0, s>>>(v, count, out, flags, K, FK, fast);
     CUDA_TRY(cudaGetLastError());
     return TENO_OK;
 }
@@ -693,23 +702,63 @@ static __device__ __align__(256) unsigned char g_rhs_scratch[TENO_RHS_STATIC_SCR
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+// Per device: the array's address and the context it was resolved in.  A
+// device reset (cudaDeviceReset) or any other context teardown unloads the
+// module holding the array, so an address is only reused while the current
+// context is the one it came from (compared by the driver's unique context id,
+// which a re-created context never repeats).
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
+CUresult (*g_ctx_get_current)(CUcontext *) = nullptr;
+CUresult (*g_ctx_get_id)(CUcontext, unsigned long long *) = nullptr;
 }  // namespace
 
-// Device address of g_rhs_scratch on the current device, resolved once per
-// device (the host-side symbol is only a stand-in, never a device address).
+// Unique id of the calling thread's current context (0 if none is current),
+// through the driver entry points the runtime hands out (no link to libcuda).
+// Called with g_scratch_mutex held.
+static int current_context_id(unsigned long long *id)
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return TENO_ECUDA;
+        g_ctx_get_current = (CUresult(*)(CUcontext *))f1;
+        g_ctx_get_id = (CUresult(*)(CUcontext, unsigned long long *))f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return TENO_ECUDA;
+    *id = 0;
+    if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return TENO_ECUDA;
+    return TENO_OK;
+}
+
+// Device address of g_rhs_scratch in the current context, resolved once per
+// device and context (the host-side symbol is only a stand-in, never a device
+// address).
 static int rhs_scratch_address(void **out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return TENO_EINVAL;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    int r = current_context_id(&id);
+    if (r) return r;
+    ScratchEntry &e = g_scratch[dev];
+    if (!e.ptr || id == 0 || e.ctx_id != id) {
         void *ptr = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_rhs_scratch));
-        g_scratch_ptr[dev] = ptr;
+        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_rhs_scratch));   // initialises the context if needed
+        if ((r = current_context_id(&id))) return r;
+        e.ptr = ptr;
+        e.ctx_id = id;
     }
-    *out = g_scratch_ptr[dev];
+    *out = e.ptr;
     return TENO_OK;
 }
 

@@ -204,6 +204,7 @@ struct teno_batch {
     const void *g_U = nullptr, *g_ws = nullptr;
     double g_cfl = 0.0;
     int g_tile = -1, g_bps = -1;
+    int g_fast = -1;            // filter switch the graph was captured with
 };
 
 namespace {
@@ -305,7 +306,7 @@ int enqueue_step(teno_batch *b, double *U, double cfl, char *ws, int tile_idx, i
     const int TF = kTiles[tile_idx];
     const int grid_f = b->num_sms * bps;
     const FastK FK = fastk_make(b->common.ct_cr, b->common.ct_alpha1, b->common.ct_alpha2);
-    const int fast = g_fast_filter;
+    const int fast = g_fast_filter && fast_filter_valid(b->common.eps_beta, b->common.eps_eta);
     for (int stg = 0; stg < 3; stg++) {
         const double *Uin = stg == 0 ? U : Us;
         if (TF == 64) {
@@ -455,7 +456,7 @@ int teno_batch_rk3_steps(teno_batch *b, double *U, int32_t nsteps, double cfl, i
     }
     if (mode != TENO_BATCH_GRAPH) return TENO_EINVAL;
     if (!b->exec || b->g_U != U || b->g_ws != ws || b->g_cfl != cfl || b->g_tile != b->tile_idx ||
-        b->g_bps != b->blocks_per_sm) {
+        b->g_bps != b->blocks_per_sm || b->g_fast != g_fast_filter) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
@@ -482,6 +483,7 @@ int teno_batch_rk3_steps(teno_batch *b, double *U, int32_t nsteps, double cfl, i
         b->g_cfl = cfl;
         b->g_tile = b->tile_idx;
         b->g_bps = b->blocks_per_sm;
+        b->g_fast = g_fast_filter;
     }
     for (int k = 0; k < nsteps; k++) CUDA_TRY(cudaGraphLaunch(b->exec, s));
     return TENO_OK;

@@ -52,6 +52,22 @@ struct FastK {
 // Filter switch (teno_set_decision_filter), process-wide.
 extern int g_fast_filter;
 
+// Whether the filter may decide for these epsilons.  Its bounds treat the
+// epsilon of Eq. scale_separation and that of the eta measure (Sec. 3.4) as
+// negligible next to indicators and squared differences of at least 2^-100
+// (in original units): the upper bounds of x_k = beta_k + eps fold eps in as
+// a relative 1.3e-10, and eta's one-sided bound as 1e-9, both of which need
+// eps <= 1e-40.  The paper's value is 1e-40; larger epsilons (or a NaN) get
+// every decision from the exact FP64 path.  Smaller ones, zero included, are
+// safe: on bit-identical values the exact path's chi is then inf/inf = NaN,
+// which the cut-off test keeps (S_p, as the shortcut answers), and every
+// other certified answer needs the small indicators above 2^-100, where
+// (beta + eps)^7 cannot underflow.
+inline bool fast_filter_valid(double eps_beta, double eps_eta)
+{
+    return eps_beta >= 0.0 && eps_beta <= 1e-40 && eps_eta >= 0.0 && eps_eta <= 1e-40;
+}
+
 // Host: constants of the filter for given C_T parameters.
 inline FastK fastk_make(double cr, double alpha1, double alpha2)
 {

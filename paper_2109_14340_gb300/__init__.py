@@ -216,8 +216,11 @@ def teno_rhs_static(p, U, rhs, dt_limiter=0.0, flags=None, stream=None):
     """teno_rhs for callers that cannot allocate: scratch comes from the
     library's fixed device array (TENO_RHS_STATIC_SCRATCH_BYTES).  Calls that
     overlap on the GPU race on that array; serialise them."""
-    need = teno_workspace_bytes(p) - 8 * (p.ndim + 2) * p.n[0] * p.n[1] * p.n[2]
-    if need > TENO_RHS_STATIC_SCRATCH_BYTES + 256:
+    teno_workspace_bytes(p)                   # validates p
+    a256 = lambda x: (x + 255) // 256 * 256
+    need = 256 + sum(a256(8 * (p.ndim + 2) * (p.n[0] + (d == 0)) * (p.n[1] + (d == 1)) *
+                          (p.n[2] + (d == 2))) for d in range(p.ndim))
+    if need > TENO_RHS_STATIC_SCRATCH_BYTES:
         raise ValueError("teno_rhs_static: this grid needs about %d bytes of scratch but the "
                          "static array holds %d; use teno_rhs with a workspace"
                          % (need, TENO_RHS_STATIC_SCRATCH_BYTES))

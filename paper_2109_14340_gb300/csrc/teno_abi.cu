@@ -32,6 +32,9 @@ struct CombineArgs {
     const double *Uk;        // stage input (whose RHS the fluxes are)
     const double *Un;        // state at t^n (RK modes)
     double *out;             // rhs (mode 0) or next stage state
+    double *P;               // RK modes: primitives of the next stage state (the
+                             // next evaluation's input, with its non-physical
+                             // cells counted here), or nullptr
     Status *st;
     int64_t n[3];
     int64_t ncell;
@@ -40,50 +43,87 @@ struct CombineArgs {
 };
 
 // L(U)_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d (Eq. approximateEq), then the
-// SSP-RK3 stage combination (Eq. Runge-kutta).  The stage input's
-// non-physical cells are counted by the x sweep, which stages every cell.
+// SSP-RK3 stage combination (Eq. Runge-kutta).  With a.P the new stage
+// state's primitives are stored for the next evaluation's sweeps and its
+// non-physical cells counted (each cell once, as that evaluation's input).
 template <int ND>
 __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
 {
     constexpr int nc = ND + 2;
     // one thread per cell; x from the block's row, y and z from the grid
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.n[0]) return;
     const int64_t y = blockIdx.y, z = blockIdx.z;
-    const int64_t id = x + a.n[0] * (y + a.n[1] * z);
-    int64_t flo[3];
-#pragma unroll
-    for (int d = 0; d < ND; d++) {
-        const int64_t fn0 = a.n[0] + (d == 0), fn1 = a.n[1] + (d == 1);
-        flo[d] = x + fn0 * (y + fn1 * z);
-    }
-    double Uc[nc];
-#pragma unroll
-    for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
-    const double dt = a.st->dt;
-#pragma unroll
-    for (int c = 0; c < nc; c++) {
-        double acc = 0.0;
+    bool bad = false;
+    if (x < a.n[0]) {
+        const int64_t id = x + a.n[0] * (y + a.n[1] * z);
+        int64_t flo[3];
 #pragma unroll
         for (int d = 0; d < ND; d++) {
-            const double *Fd = a.F[d] + c * a.nfaces[d];
-            const int64_t xd = (d == 0) ? x : (d == 1 ? y : z);
-            const int64_t fr = (a.wrap[d] && xd == a.n[d] - 1) ? flo[d] - xd * a.fstride[d]
-                                                                : flo[d] + a.fstride[d];
-            const double t = (Fd[fr] - Fd[flo[d]]) * a.inv_dx[d];
-            acc = acc - t;
+            const int64_t fn0 = a.n[0] + (d == 0), fn1 = a.n[1] + (d == 1);
+            flo[d] = x + fn0 * (y + fn1 * z);
         }
-        double o;
-        if (a.mode == 0) {
-            o = acc;
-        } else {
-            const double t = Uc[c] + dt * acc;
-            if (a.mode == 1) o = t;
-            else if (a.mode == 2) o = 0.75 * a.Un[c * a.ncell + id] + 0.25 * t;
-            else o = (1.0 / 3.0) * a.Un[c * a.ncell + id] + (2.0 / 3.0) * t;
+        double Uc[nc], Uo[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Uc[c] = a.Uk[c * a.ncell + id];
+        const double dt = a.st->dt;
+#pragma unroll
+        for (int c = 0; c < nc; c++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int d = 0; d < ND; d++) {
+                const double *Fd = a.F[d] + c * a.nfaces[d];
+                const int64_t xd = (d == 0) ? x : (d == 1 ? y : z);
+                const int64_t fr = (a.wrap[d] && xd == a.n[d] - 1) ? flo[d] - xd * a.fstride[d]
+                                                                    : flo[d] + a.fstride[d];
+                const double t = (Fd[fr] - Fd[flo[d]]) * a.inv_dx[d];
+                acc = acc - t;
+            }
+            double o;
+            if (a.mode == 0) {
+                o = acc;
+            } else {
+                const double t = Uc[c] + dt * acc;
+                if (a.mode == 1) o = t;
+                else if (a.mode == 2) o = 0.75 * a.Un[c * a.ncell + id] + 0.25 * t;
+                else o = (1.0 / 3.0) * a.Un[c * a.ncell + id] + (2.0 / 3.0) * t;
+            }
+            a.out[c * a.ncell + id] = o;
+            Uo[c] = o;
         }
-        a.out[c * a.ncell + id] = o;
+        if (a.P) {
+            CellQ<ND> q;
+            cell_quantities<ND, 0>(Uo, a.K, q);
+            store_prims<ND>(q, a.P, a.ncell, id);
+            bad = nonphysical_cell<ND>(Uo[0], q);
+        }
     }
+    if (a.P) {            // every lane of the warp is here (no early return)
+        const unsigned nb = __popc(__ballot_sync(0xffffffffu, bad));
+        if ((threadIdx.x & 31) == 0 && nb) atomicAdd(&a.st->nonphys, (unsigned long long)nb);
+    }
+}
+
+// Primitives of a right-hand-side input (store_prims), read by every sweep of
+// the evaluation instead of recomputing them per staged cell; counts the
+// input's non-physical cells (each cell once).
+template <int ND>
+__global__ void __launch_bounds__(256) prims_kernel(const double *U, int64_t ncell, Consts K,
+                                                    double *P, Status *st)
+{
+    constexpr int nc = ND + 2;
+    unsigned long long bad = 0;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < ncell;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        double Uc[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) Uc[c] = U[c * ncell + id];
+        CellQ<ND> q;
+        cell_quantities<ND, 0>(Uc, K, q);
+        store_prims<ND>(q, P, ncell, id);
+        if (nonphysical_cell<ND>(Uc[0], q)) bad++;
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&st->nonphys, bad);
 }
 
 // A_d = max over cells of |u_d| + c, accumulated as bit patterns (the
@@ -203,7 +243,7 @@ static int64_t face_grid(const teno_params *p, int d)
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t status, flux[3], stage, total;
+    size_t status, flux[3], stage, prims, total;
 };
 
 static Layout layout(const teno_params *p)
@@ -219,6 +259,8 @@ static Layout layout(const teno_params *p)
     }
     L.stage = off;
     off += align256(sizeof(double) * (size_t)nc * ncells(p));
+    L.prims = off;
+    off += align256(sizeof(double) * (size_t)(p->ndim + 4) * ncells(p));
     L.total = off;
     return L;
 }
@@ -324,6 +366,24 @@ static cudaError_t launch_wave_max(const teno_params *p, const double *U, Status
     return cudaGetLastError();
 }
 
+// Primitives of U into the workspace's primitive rows (non-physical cells
+// counted); returns their address.
+static cudaError_t launch_prims(const teno_params *p, const double *U, char *ws, cudaStream_t s,
+                                double **P_out)
+{
+    const Layout L = layout(p);
+    Status *st = (Status *)(ws + L.status);
+    double *P = (double *)(ws + L.prims);
+    const Consts K = consts_of(p);
+    const int64_t N = ncells(p);
+    const int blk = 256, grd = grid_for(N, blk);
+    if (p->ndim == 1) prims_kernel<1><<<grd, blk, 0, s>>>(U, N, K, P, st);
+    else if (p->ndim == 2) prims_kernel<2><<<grd, blk, 0, s>>>(U, N, K, P, st);
+    else prims_kernel<3><<<grd, blk, 0, s>>>(U, N, K, P, st);
+    *P_out = P;
+    return cudaGetLastError();
+}
+
 // Event record of the face-sweep launches (teno_profile_*).
 struct ProfileRecord {
     bool on = false;
@@ -349,9 +409,13 @@ static cudaError_t profile_mark(int which, int slot, cudaStream_t s)
 }
 
 // One right-hand-side evaluation of Uk into the face buffers, then combine.
+// P_in: primitives of Uk (prims_kernel or the previous combine), read by the
+// sweeps, or nullptr (the sweeps compute them and the x sweep counts the
+// non-physical cells); P_out: where the combine stores the primitives of
+// its output for the next stage, or nullptr.
 static int stage(const teno_params *p, const double *Uk, const double *Un, double *out, int mode,
                  double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s,
-                 const uint8_t *frozen = nullptr)
+                 const uint8_t *frozen, const double *P_in, double *P_out)
 {
     const Layout L = layout(p);
     Status *st = (Status *)(ws + L.status);
@@ -372,6 +436,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     for (int d = 0; d < nd; d++) {
         FaceArgs a;
         a.U = Uk;
+        a.P = P_in;
         a.F = (double *)(ws + L.flux[d]);
         a.flags = fl;
         a.frozen = fz;
@@ -388,7 +453,8 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.lam = &st->lam[d];
         a.fast = filter_on(p);
         a.skip_last = (p->bc_lo[d] == TENO_BC_PERIODIC && !fl && !fz) ? 1 : 0;
-        a.count_cells = (d == 0);                 // the x sweep counts the stage input's cells
+        a.count_cells = (d == 0 && !P_in);        // the x sweep counts the stage input's cells
+                                                  // unless its primitives were stored
         a.exact_count = g_prof.on ? g_prof.exact : nullptr;
         a.FK = fastk_of(p);
         a.K = K;
@@ -418,6 +484,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     c.Uk = Uk;
     c.Un = Un;
     c.out = out;
+    c.P = P_out;
     c.st = st;
     for (int k = 0; k < 3; k++) c.n[k] = p->n[k];
     c.ncell = ncells(p);
@@ -487,7 +554,10 @@ int teno_rhs(const teno_params *p, const double *U, double *rhs, double dt_limit
     if (U == rhs) return TENO_EINVAL;
     if (ws_bytes < layout(p).total) return TENO_EINVAL;
     if (p->limiter && !(dt_limiter >= 0.0)) return TENO_EINVAL;
-    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)ws, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    double *P = nullptr;
+    CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)ws, s, nullptr, P, nullptr);
 }
 
 int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_device,
@@ -501,10 +571,13 @@ int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_d
     const Layout L = layout(p);
     double *Us = (double *)((char *)ws + L.stage);
     cudaStream_t s = (cudaStream_t)stream;
-    // U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U = 1/3 U + 2/3 (U2 + dt L(U2))
-    if ((r = stage(p, U, U, Us, 1, dt, dt_device, nullptr, (char *)ws, s))) return r;
-    if ((r = stage(p, Us, U, Us, 2, dt, dt_device, nullptr, (char *)ws, s))) return r;
-    return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s);
+    // U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U = 1/3 U + 2/3 (U2 + dt L(U2));
+    // each stage's combine stores the primitives of the next stage's input
+    double *P = nullptr;
+    CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+    if ((r = stage(p, U, U, Us, 1, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, P))) return r;
+    if ((r = stage(p, Us, U, Us, 2, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, P))) return r;
+    return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, nullptr);
 }
 
 int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
@@ -518,9 +591,11 @@ int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1,
     teno_flags_bytes(p, &flb);
     cudaStream_t s = (cudaStream_t)stream;
     // the stages of teno_rk3_step, with the stage states and decision records kept
-    if ((r = stage(p, U, U, U1, 1, dt, nullptr, flags, (char *)ws, s))) return r;
-    if ((r = stage(p, U1, U, U2, 2, dt, nullptr, flags + flb, (char *)ws, s))) return r;
-    return stage(p, U2, U, U, 3, dt, nullptr, flags + 2 * flb, (char *)ws, s);
+    double *P = nullptr;
+    CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+    if ((r = stage(p, U, U, U1, 1, dt, nullptr, flags, (char *)ws, s, nullptr, P, P))) return r;
+    if ((r = stage(p, U1, U, U2, 2, dt, nullptr, flags + flb, (char *)ws, s, nullptr, P, P))) return r;
+    return stage(p, U2, U, U, 3, dt, nullptr, flags + 2 * flb, (char *)ws, s, nullptr, P, nullptr);
 }
 
 int teno_rhs_frozen(const teno_params *p, const double *U, double *rhs, double dt_limiter,
@@ -531,8 +606,11 @@ int teno_rhs_frozen(const teno_params *p, const double *U, double *rhs, double d
     if (check_ptr(U) || check_ptr(rhs) || check_ptr(ws) || !decisions || U == rhs) return TENO_EINVAL;
     if (ws_bytes < layout(p).total) return TENO_EINVAL;
     if (p->limiter && !(dt_limiter >= 0.0)) return TENO_EINVAL;
-    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, nullptr, (char *)ws, (cudaStream_t)stream,
-                 decisions);
+    cudaStream_t s = (cudaStream_t)stream;
+    double *P = nullptr;
+    CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, nullptr, (char *)ws, s, decisions, P,
+                 nullptr);
 }
 
 int teno_rk3_step_frozen(const teno_params *p, double *U, double dt, const uint8_t *decisions,
@@ -547,9 +625,13 @@ int teno_rk3_step_frozen(const teno_params *p, double *U, double dt, const uint8
     const Layout L = layout(p);
     double *Us = (double *)((char *)ws + L.stage);
     cudaStream_t s = (cudaStream_t)stream;
-    if ((r = stage(p, U, U, Us, 1, dt, nullptr, nullptr, (char *)ws, s, decisions))) return r;
-    if ((r = stage(p, Us, U, Us, 2, dt, nullptr, nullptr, (char *)ws, s, decisions + flb))) return r;
-    return stage(p, Us, U, U, 3, dt, nullptr, nullptr, (char *)ws, s, decisions + 2 * flb);
+    double *P = nullptr;
+    CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+    if ((r = stage(p, U, U, Us, 1, dt, nullptr, nullptr, (char *)ws, s, decisions, P, P))) return r;
+    if ((r = stage(p, Us, U, Us, 2, dt, nullptr, nullptr, (char *)ws, s, decisions + flb, P, P)))
+        return r;
+    return stage(p, Us, U, U, 3, dt, nullptr, nullptr, (char *)ws, s, decisions + 2 * flb, P,
+                 nullptr);
 }
 
 int teno_cfl_dt(const teno_params *p, const double *U, double cfl, double *dt_device,
@@ -778,5 +860,6 @@ extern "C" int teno_rhs_static(const teno_params *p, const double *U, double *rh
     // The array keeps the previous call's contents: zero the status header
     // (counters and reduction slots) before use.
     CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(Status), s));
-    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)scratch, s);
+    return stage(p, U, U, rhs, 0, dt_limiter, nullptr, flags, (char *)scratch, s, nullptr, nullptr,
+                 nullptr);
 }

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         const BatchProb d = probs[p];
         FaceArgs a;
         a.U = U + d.u_off;
+        a.P = nullptr;                      // primitives computed while staging
         a.F = F + d.f_off;
         a.flags = nullptr;
         a.frozen = nullptr;

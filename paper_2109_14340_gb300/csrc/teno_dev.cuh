@@ -348,6 +348,63 @@ __device__ __forceinline__ void cell_quantities(const double (&Uc)[ND + 2], cons
     q.F[nc - 1] = q.u[D] * Ep;
 }
 
+// Primitive quantities of a cell kept between kernels: [NP][ncell] with
+// rows u_0 .. u_{ND-1}, p, c, H, sqrt(rho) (the values cell_quantities
+// computes).  Written once per right-hand-side input by prims_kernel or the
+// previous stage's combine, read by every sweep of that evaluation.
+template <int ND>
+struct PrimRows {
+    static constexpr int P = ND, C = ND + 1, H = ND + 2, SR = ND + 3, NP = ND + 4;
+};
+
+template <int ND>
+__device__ __forceinline__ void store_prims(const CellQ<ND> &q, double *P, int64_t ncell, int64_t id)
+{
+    using R = PrimRows<ND>;
+#pragma unroll
+    for (int a = 0; a < ND; a++) P[a * ncell + id] = q.u[a];
+    P[R::P * ncell + id] = q.p;
+    P[R::C * ncell + id] = q.c;
+    P[R::H * ncell + id] = q.H;
+    P[R::SR * ncell + id] = q.sr;
+}
+
+// cell_quantities of a cell whose primitives were stored by store_prims: the
+// flux along D is formed from them with the same operations, so every value
+// is bitwise the one cell_quantities gives (rinv is not recovered).
+template <int ND, int D>
+__device__ __forceinline__ void cell_from_prims(const double (&Uc)[ND + 2], const double *P,
+                                                int64_t ncell, int64_t id, CellQ<ND> &q)
+{
+    using R = PrimRows<ND>;
+    constexpr int nc = ND + 2;
+#pragma unroll
+    for (int c = 0; c < nc; c++) q.U[c] = Uc[c];
+#pragma unroll
+    for (int a = 0; a < ND; a++) q.u[a] = P[a * ncell + id];
+    q.p = P[R::P * ncell + id];
+    q.c = P[R::C * ncell + id];
+    q.H = P[R::H * ncell + id];
+    q.sr = P[R::SR * ncell + id];
+    q.rinv = 0.0;
+    const double Ep = Uc[nc - 1] + q.p;
+    const double md = Uc[1 + D];
+    q.F[0] = md;
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+        q.F[1 + a] = md * q.u[a];
+        if (a == D) q.F[1 + a] = q.F[1 + a] + q.p;
+    }
+    q.F[nc - 1] = q.u[D] * Ep;
+}
+
+// The non-physical test of a cell (rho <= 0, p <= 0, non-finite c or H).
+template <int ND>
+__device__ __forceinline__ bool nonphysical_cell(double rho, const CellQ<ND> &q)
+{
+    return !(rho > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H);
+}
+
 // Pressure of a conserved state (used by the limiter).
 template <int ND>
 __device__ __forceinline__ double pressure_of(const double (&Uc)[ND + 2], double gm1)

@@ -6,7 +6,10 @@
 // Tiling: a block owns TF consecutive faces along the sweep axis D for TP
 // pencils adjacent in x.  It stages the TF + 2H - 1 cells those faces touch
 // (ghost cells resolved by the boundary rules of App. A) in shared memory as
-// per-cell primitive quantities, then one thread computes one face.
+// per-cell primitive quantities, then one thread computes one face.  U and F
+// are staged halved (exact: a power of two), so that the projections give
+// the halved characteristic variables and fluxes w/2, g/2 directly and the
+// split fluxes (g +- alpha w)/2 need no further scaling.
 #pragma once
 
 #include "teno_dev.cuh"
@@ -16,6 +19,8 @@ namespace teno {
 
 struct FaceArgs {
     const double *U;       // state, [nc][ncell]
+    const double *P;       // primitives of U ([PrimRows::NP][ncell], store_prims) or
+                           // nullptr: computed while staging
     double *F;             // face fluxes of direction D, [nc][nfaces]
     uint8_t *flags;        // decision record of direction D or nullptr
     const uint8_t *frozen; // recorded decisions to apply instead of deciding, or nullptr
@@ -189,23 +194,29 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
-        if (rule) {
-            // boundary-face index among the faces of this side (other axes, x fastest)
-            const int64_t m = a.ncell / nD;
-            const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
-            apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
-        }
         CellQ<ND> q;
-        cell_quantities<ND, D>(Uc, a.K, q);
+        if (!rule && a.P) {
+            cell_from_prims<ND, D>(Uc, a.P, a.ncell, id, q);      // stored for this input
+        } else {
+            if (rule) {
+                // boundary-face index among the faces of this side (other axes, x fastest)
+                const int64_t m = a.ncell / nD;
+                const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
+                apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
+            }
+            cell_quantities<ND, D>(Uc, a.K, q);
+        }
         if (a.count_cells) {
             // interior cells of this tile's own face range: each cell once
             const int64_t ci = f0 - H + j;
-            if (ci >= f0 && ci < f0 + TF && ci < nD &&
-                (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H)))
+            if (ci >= f0 && ci < f0 + TF && ci < nD && nonphysical_cell<ND>(Uc[0], q))
                 atomicAdd(&a.st->nonphys, 1ull);
         }
 #pragma unroll
-        for (int c = 0; c < nc; c++) { SQ(SL::QU + c, j, p) = q.U[c]; SQ(SL::QF + c, j, p) = q.F[c]; }
+        for (int c = 0; c < nc; c++) {
+            SQ(SL::QU + c, j, p) = 0.5 * q.U[c];
+            SQ(SL::QF + c, j, p) = 0.5 * q.F[c];
+        }
 #pragma unroll
         for (int k = 0; k < ND; k++) SQ(SL::QV + k, j, p) = q.u[k];
         SQ(SL::QH, j, p) = q.H;
@@ -288,8 +299,9 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         double lrow[nc];
         l_row<ND, D>(rs, k, lrow);
         const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
-        const double ha = 0.5 * alpha;
-        double w[W], hg[W];
+        // hw = w/2 = l.(U/2), hg = g/2 = l.(F/2) from the halved staged values:
+        // every product and sum is the unhalved one scaled by 1/2, exactly
+        double hw[W], hg[W];
 #pragma unroll
         for (int j = 0; j < W; j++) {
             double wv, gv;
@@ -305,18 +317,18 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                     gv = fma(lrow[c], SQ(SL::QF + c, fo + j, p), gv);
                 }
             }
-            w[j] = wv;
-            hg[j] = 0.5 * gv;
+            hw[j] = wv;
+            hg[j] = gv;
         }
 #pragma unroll 1
         for (int s = 0; s < 2; s++) {
             // f+ on offsets m -> cell i+m; f- mirrored: offset m -> cell i+1-m.
-            // v = (g +- alpha w)/2, as fma(+-alpha/2, w, g/2) (exact halving).
-            const double sa = s ? -ha : ha;
+            // v = (g +- alpha w)/2 = fma(+-alpha, w/2, g/2), rounded once.
+            const double sa = s ? -alpha : alpha;
             double v[W];
 #pragma unroll
             for (int kk = 0; kk < W; kk++) {
-                const double wk = s ? w[W - 1 - kk] : w[kk];
+                const double wk = s ? hw[W - 1 - kk] : hw[kk];
                 const double gk = s ? hg[W - 1 - kk] : hg[kk];
                 v[kk] = fma(sa, wk, gk);
             }
@@ -432,9 +444,12 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         double FL[nc], dF[nc], UL[nc], UR[nc], dUL[nc], dUR[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) {
-            const double Ul = SQ(SL::QU + c, jl, p), Ur = SQ(SL::QU + c, jr, p);
-            const double Fl = SQ(SL::QF + c, jl, p), Fr = SQ(SL::QF + c, jr, p);
-            FL[c] = 0.5 * ((Fl + Fr) - af * (Ur - Ul));
+            // staged halves: FL = (F_l + F_r)/2 - af (U_r - U_l)/2 exactly as
+            // ((F_l + F_r) - af (U_r - U_l)) / 2
+            const double hUl = SQ(SL::QU + c, jl, p), hUr = SQ(SL::QU + c, jr, p);
+            const double hFl = SQ(SL::QF + c, jl, p), hFr = SQ(SL::QF + c, jr, p);
+            const double Ul = 2.0 * hUl, Ur = 2.0 * hUr, Fl = 2.0 * hFl, Fr = 2.0 * hFr;
+            FL[c] = (hFl + hFr) - af * (hUr - hUl);
             dF[c] = Fo[c] - FL[c];
             UL[c] = Ul - lam2 * (FL[c] - Fl);
             UR[c] = Ur + lam2 * (FL[c] - Fr);

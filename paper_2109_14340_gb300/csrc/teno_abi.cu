@@ -218,7 +218,7 @@ __global__ void recon_kernel(const double *v, int64_t count, double *out, uint8_
         for (int m = 0; m < W; m++) sh[m] = vv[m] - vv[H - 1];
         uint8_t fl = 0;
         double r;
-        if (fast && fast_decide<H>(vv, sh, FK, fl)) r = decided_value<H>(vv, fl);
+        if (fast && fast_decide<H>(vv, sh, FK, fl, flags != nullptr)) r = decided_value<H>(vv, fl);
         else r = teno_recon<H>(vv, K, fl);
         out[i] = r;
         if (flags) flags[i] = fl;

@@ -342,7 +342,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
-                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl);
+                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl, a.flags != nullptr);
                 // the largest stencil accepted (S6 as bits 0-4 zero).  Kept
                 // inline: the same test through a helper function made the 8-
                 // and 10-point sweeps 4-14 % slower (same registers, other code).

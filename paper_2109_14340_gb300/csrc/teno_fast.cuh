@@ -45,6 +45,8 @@ struct FastK {
     float cr_inv_lo, cr_inv_hi;  // 1 / C_r rounded down / up
     float alpha1, alpha2;
     int nexp_smooth;             // [beta] at m = 0, as the exact path computes it
+    int nexp_min;                // [beta] at g = 0: no exponent the exact path computes
+                                 // is smaller (g >= 0 and rounding is monotone)
     float thr[23];               // thr[n] <= 1 / (10^-n (1 + 2^-16)) - 1
     float thr_rej[23];           // thr_rej[n] >= 1 / (10^-n (1 - 2^-16)) - 1
 };
@@ -80,6 +82,9 @@ inline FastK fastk_make(double cr, double alpha1, double alpha2)
     const double bct = alpha1 - alpha2 * (1.0 - 1.0);
     const double fl = floor(bct);
     F.nexp_smooth = fl < 0.0 ? 0 : (fl > 22.0 ? 22 : (int)fl);
+    const double bmin = alpha1 - alpha2 * (1.0 - 0.0);
+    const double flm = floor(bmin);
+    F.nexp_min = flm < 0.0 ? 0 : (flm > 22.0 ? 22 : (int)flm);
     for (int n = 0; n < 23; n++) {
         const double t = 1.0 / (pow(10.0, -n) * (1.0 + 1.0 / 65536.0)) - 1.0;
         // round down (toward -inf), then one more step: a safe lower bound
@@ -273,11 +278,12 @@ __device__ __forceinline__ int select_large(const float (&f)[2 * H], float tiny2
 }
 
 // The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
-// (s[H-1] == 0).  Returns true with the decision byte (the exact path's
-// encoding) when every decision is certain.
+// (s[H-1] == 0); need_ct: the caller records the decision byte, so its C_T
+// exponent must be known.  Returns true with the decision byte (the exact
+// path's encoding) when every decision is certain.
 template <int H>
 __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const double (&s)[2 * H],
-                                            const FastK &F, uint8_t &flag)
+                                            const FastK &F, uint8_t &flag, bool need_ct)
 {
     constexpr int W = 2 * H;
 #define SV(m) s[(m) + H - 1]
@@ -317,6 +323,53 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const float eo = ev < -900 ? 0.0f : __uint_as_float((unsigned)(max(ev - emax - 50, -126) + 127) << 23);
 #define FF(m) f[(m) + H - 1]
 
+    // Small indicators on the shifted values (s_0 = 0).
+    float b0, e0, b1, e1, b2, e2;
+    {
+        const float slack = 2.0f * z100 + 4.0f * eo;
+        const float a = FF(-1) - FF(1);
+        const float ea = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(a) + slack;
+        const float b = FF(-1) + FF(1);
+        const float eb = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b0, e0);
+    }
+    {
+        const float slack = 5.0f * z100 + 8.0f * eo;
+        const float a = FF(2) - 4.0f * FF(1);
+        const float ea = u23 * (fabsf(FF(2)) + 4.0f * fabsf(FF(1))) + u24 * fabsf(a) + slack;
+        const float b = FF(2) - 2.0f * FF(1);
+        const float eb = u23 * (fabsf(FF(2)) + 2.0f * fabsf(FF(1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b1, e1);
+    }
+    {
+        const float slack = 5.0f * z100 + 8.0f * eo;
+        const float a = FF(-2) - 4.0f * FF(-1);
+        const float ea = u23 * (fabsf(FF(-2)) + 4.0f * fabsf(FF(-1))) + u24 * fabsf(a) + slack;
+        const float b = FF(-2) - 2.0f * FF(-1);
+        const float eb = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(b) + slack;
+        small_beta(a, ea, b, eb, b2, e2);
+    }
+    // x_k = beta_k + eps: lower bounds (eps dropped) and upper bounds (eps
+    // < 1.3e-10 tiny2 <= 1.3e-10 x_k folded into the factor).
+    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;
+    if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
+    const float X0 = (b0 + e0) * (1.0f + 1e-6f), X1 = (b1 + e1) * (1.0f + 1e-6f);
+    const float X2 = (b2 + e2) * (1.0f + 1e-6f);
+
+    // Without a decision record the exponent only matters when S_p is not
+    // accepted: accept it at once when chi_p >= C_T holds for the largest
+    // C_T the parameters allow (the exponent's lower bound, at g = 0), which
+    // leaves the eta measure out for most reconstructions.  The C_T bits of
+    // the byte are then zero (the byte is not stored).
+    if (!need_ct) {
+        float lo, hi;
+        beta_large_bounds<H, H>(f, lo, hi);
+        if (pow7_sum(fmaxf(hi, tiny2), x0, x1, x2, true) <= F.thr[F.nexp_min]) {
+            flag = (uint8_t)large_code(H);
+            return true;
+        }
+    }
+
     // eta measure over cells -1..2 from the differences Delta_{m+1/2}, m=-2..2.
     float dl[5], el[5];
     bool zl[5];
@@ -355,39 +408,6 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     }
     const uint8_t fct = (uint8_t)(((nexp - 7) & 7) << 5);
     const float thr = F.thr[nexp], thr_rej = F.thr_rej[nexp];
-
-    // Small indicators on the shifted values (s_0 = 0).
-    float b0, e0, b1, e1, b2, e2;
-    {
-        const float slack = 2.0f * z100 + 4.0f * eo;
-        const float a = FF(-1) - FF(1);
-        const float ea = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(a) + slack;
-        const float b = FF(-1) + FF(1);
-        const float eb = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b0, e0);
-    }
-    {
-        const float slack = 5.0f * z100 + 8.0f * eo;
-        const float a = FF(2) - 4.0f * FF(1);
-        const float ea = u23 * (fabsf(FF(2)) + 4.0f * fabsf(FF(1))) + u24 * fabsf(a) + slack;
-        const float b = FF(2) - 2.0f * FF(1);
-        const float eb = u23 * (fabsf(FF(2)) + 2.0f * fabsf(FF(1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b1, e1);
-    }
-    {
-        const float slack = 5.0f * z100 + 8.0f * eo;
-        const float a = FF(-2) - 4.0f * FF(-1);
-        const float ea = u23 * (fabsf(FF(-2)) + 4.0f * fabsf(FF(-1))) + u24 * fabsf(a) + slack;
-        const float b = FF(-2) - 2.0f * FF(-1);
-        const float eb = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b2, e2);
-    }
-    // x_k = beta_k + eps: lower bounds (eps dropped) and upper bounds (eps
-    // < 1.3e-10 tiny2 <= 1.3e-10 x_k folded into the factor).
-    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;
-    if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
-    const float X0 = (b0 + e0) * (1.0f + 1e-6f), X1 = (b1 + e1) * (1.0f + 1e-6f);
-    const float X2 = (b2 + e2) * (1.0f + 1e-6f);
 
     // Targeted selection, largest group first (Sec. 3.3).
     const int sel = select_large<H, H>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);

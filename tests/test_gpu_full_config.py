@@ -232,10 +232,15 @@ def test_final_time_2d_200_steps():
 # --------------------------------------------------------------------------
 
 def _rhs_both_ways(s, Ud):
+    """RHS and record with the filter on and off; the RHS without a record
+    (where the filter may accept S_p without the C_T exponent) must equal
+    them both ways too."""
     r_on, f_on = s.rhs(Ud, flags=True)
+    assert torch.equal(s.rhs(Ud), r_on)
     T.teno_set_decision_filter(False)
     try:
         r_off, f_off = s.rhs(Ud, flags=True)
+        assert torch.equal(s.rhs(Ud), r_off)
     finally:
         T.teno_set_decision_filter(True)
     return r_on, f_on, r_off, f_off

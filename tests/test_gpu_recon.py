@@ -31,15 +31,17 @@ def oracle_batch(scheme, V):
     return out, fl
 
 
-def gpu_batch(scheme, V, fast):
+def gpu_batch(scheme, V, fast, with_flags=True):
+    """Values and decision bytes (None without a record: the filter may then
+    accept S_p for every C_T the parameters allow without the eta measure)."""
     p = T.teno_params_init(scheme=scheme)
     T.teno_set_decision_filter(fast)
     try:
         v = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
         out = torch.empty(len(V), dtype=torch.float64, device=DEV)
-        fl = torch.empty(len(V), dtype=torch.uint8, device=DEV)
+        fl = torch.empty(len(V), dtype=torch.uint8, device=DEV) if with_flags else None
         T.teno_reconstruct(p, v, out, fl)
-        return out.cpu().numpy(), fl.cpu().numpy()
+        return out.cpu().numpy(), (fl.cpu().numpy() if with_flags else None)
     finally:
         T.teno_set_decision_filter(True)
 
@@ -168,6 +170,9 @@ def test_reconstruction_matches_oracle(scheme):
         out, fl = gpu_batch(scheme, V, fast)
         bad = np.nonzero((fl != rfl) | (out.view(np.int64) != ref.view(np.int64)))[0]
         assert bad.size == 0, (fast, bad[:10], fl[bad[:5]], rfl[bad[:5]])
+        out, _ = gpu_batch(scheme, V, fast, with_flags=False)
+        bad = np.nonzero(out.view(np.int64) != ref.view(np.int64))[0]
+        assert bad.size == 0, (fast, "no record", bad[:10])
 
 
 @pytest.mark.parametrize("scheme", [8, 10, 12])

@@ -53,10 +53,14 @@ def parse_args():
     ap.add_argument("--no-noh", action="store_true")
     ap.add_argument("--no-teno12", action="store_true",
                     help="skip the TENO12-AA line (same workload, twelve-point scheme)")
+    ap.add_argument("--no-teno8", action="store_true",
+                    help="skip the TENO8-AA line (same workload, eight-point scheme)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint workload and print its record (profiling)")
     ap.add_argument("--adjoint-n", type=int, default=512)
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--fd-directions", type=int, default=16,
+                    help="seeded directions of the adjoint's central-difference check")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -68,12 +72,16 @@ def parse_args():
 # ---------------------------------------------------------------------------
 
 def flops_per_cell_sweep(nd):
-    # primitive variables, sound speed, enthalpy, sqrt(rho), physical flux
-    # (4 nd + 11) and the three characteristic speeds |u-c|, |u+c|, |u|+c
+    # the plain method's per-cell work: primitive variables, sound speed,
+    # enthalpy, sqrt(rho), physical flux (4 nd + 11) and the three
+    # characteristic speeds |u-c|, |u+c|, |u|+c
     return 4 * nd + 11 + 3
 
 
 def flops_face_fixed(nd, H):
+    """The plain method's fixed FP64 work per face (Roe average,
+    eigenvectors, projection of the 2H stencil cells, splitting,
+    back-projection)."""
     nc = nd + 2
     roe = 6 * nd + 17
     eig = 3 * nd + 14
@@ -81,6 +89,102 @@ def flops_face_fixed(nd, H):
     split = nc * 2 * H * 6
     back = nc * (2 * nc - 1) + nc
     return roe + eig + proj + split + back
+
+
+# FP64 instructions (DADD, DMUL, DFMA) of one double division and one double
+# square root as the compiler expands them on sm_103a, measured with ncu from
+# the instruction counts of prims_kernel (one division, two square roots per
+# cell) and wave_max_kernel (one of each) minus their other operations.
+KDIV = {"dadd": 0.0, "dmul": 0.0, "dfma": 5.0}
+KSQRT = {"dadd": 0.0, "dmul": 3.0, "dfma": 5.0}
+FP64_LANES_PER_CLK_SM = 2        # FP64 pipe: 2 lanes per SM per clock (DADD, DMUL or DFMA)
+
+
+def _acc(tot, add=0.0, mul=0.0, fma=0.0, div=0.0, sqrt=0.0, w=1.0):
+    tot["dadd"] += w * (add + div * KDIV["dadd"] + sqrt * KSQRT["dadd"])
+    tot["dmul"] += w * (mul + div * KDIV["dmul"] + sqrt * KSQRT["dmul"])
+    tot["dfma"] += w * (fma + div * KDIV["dfma"] + sqrt * KSQRT["dfma"])
+
+
+def face_fp64_instructions(nd, H, hist, exact_frac, tf=32, stored_prims=True):
+    """FP64 instructions the face-sweep kernel executes per face, by kind,
+    following its code: staged cells formed from the stored primitives
+    (flux, halving, speeds), Roe average and eigenvector rows, projection of
+    the halved staged values, one fma per split value, the 2H - 1 shifted
+    values the decision filter reads, each reconstruction's value formula
+    for its decided outcome (hist: fractions of fallback, S3 .. S_H) or the
+    whole method on the exact path (exact_frac), and the back-projection.
+    The filter's own single-precision and integer work is not FP64."""
+    nc, W = nd + 2, 2 * H
+    nrec = 2 * nc
+    t = {"dadd": 0.0, "dmul": 0.0, "dfma": 0.0}
+    staged = (tf + W - 1) / tf
+    if stored_prims:
+        _acc(t, add=5, mul=nd + 1 + 2 * nc, w=staged)                   # staged cells
+    else:                                # batched mode: primitives computed while staging
+        _acc(t, add=6, mul=2 * nd + 7 + 2 * nc, fma=nd - 1, div=1, sqrt=2, w=staged)
+    _acc(t, add=2, mul=2 * nd + 12, fma=2 * nd, div=2, sqrt=1)         # Roe state
+    _acc(t, add=5, mul=5 * nd + 2)                                     # eigenvector rows
+    _acc(t, mul=3 * W * 2, fma=3 * W * 2 * (nc - 1))                   # acoustic, entropy
+    _acc(t, add=(nd - 1) * W * 2, mul=(nd - 1) * W * 2)                # shear fields
+    _acc(t, fma=nc * 2 * W)                                            # split values
+    _acc(t, add=nrec * (W - 1))                                        # shifted values
+    for sel in range(5):                                               # decided values
+        f = hist[sel] * nrec * (1.0 - exact_frac)
+        if sel == 0:
+            _acc(t, add=6, mul=8, fma=2, div=3, w=f)
+        else:
+            _acc(t, mul=1, fma=2 * (sel + 2) - 1, w=f)
+    _acc(t, add=nc + nd + 3, mul=nc + 1, fma=(nd - 1) + 2 * nc)        # back-projection
+    exact = exact_frac * nrec * sum(hist[s] * recon_flops(H, s) for s in range(5))
+    return t, exact
+
+
+def executed_fp64_per_face(hist, exact_frac, nd, H):
+    """FP64 flops the face kernel executes per face (add/mul 1, fma 2),
+    from face_fp64_instructions."""
+    t, exact = face_fp64_instructions(nd, H, hist, exact_frac)
+    return t["dadd"] + t["dmul"] + 2.0 * t["dfma"] + exact
+
+
+def executed_fp64_instr_per_face(hist, exact_frac, nd, H):
+    """FP64 instructions (thread level: DADD, DMUL, DFMA, each one slot of
+    the FP64 pipe) the face kernel executes per face; the rare exact-path
+    reconstructions counted as if all their flops were fmas (a lower bound)."""
+    t, exact = face_fp64_instructions(nd, H, hist, exact_frac)
+    return t["dadd"] + t["dmul"] + t["dfma"] + 0.5 * exact
+
+
+def fp64_roofline(hist, exact_frac, nd, H, faces_per_launch, avg_launch_s, method_fpf):
+    """The face kernel against the FP64 pipe: executed FP64 instructions per
+    second over the pipe's 2 lanes per SM per clock (the binding resource),
+    with the same work in flops against the DFMA peak, and the plain
+    method's op count over the same time."""
+    ipf = executed_fp64_instr_per_face(hist, exact_frac, nd, H)
+    fpf = executed_fp64_per_face(hist, exact_frac, nd, H)
+    peak_i = N_SM * FP64_LANES_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    peak_f = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    ach_i = ipf * faces_per_launch / avg_launch_s / 1e9
+    ach_f = fpf * faces_per_launch / avg_launch_s / 1e12
+    ach_m = method_fpf * faces_per_launch / avg_launch_s / 1e12
+    return {
+        "bound": "alu", "kernel": "face_kernel (x/y/z face sweeps)",
+        "achieved": ach_i, "peak": peak_i, "unit": "G FP64 instr/s", "frac": ach_i / peak_i,
+        "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2.07 GHz (DADD, DMUL and DFMA "
+                       "each take one lane slot)",
+        "counted": "FP64 instructions executed per face, counted from the kernel's code with "
+                   "the live decision mix and exact-path fraction (div/sqrt expansions measured "
+                   "with ncu); ncu counts about 3 % more (sign and absolute-value operations)",
+        "fp64_instr_per_face": ipf,
+        "flops": {"achieved": ach_f, "peak": peak_f, "unit": "TFLOP/s", "frac": ach_f / peak_f,
+                  "fp64_flops_per_face": fpf,
+                  "note": "the same work in flops (fma 2) against the all-DFMA peak"},
+        "method_equivalent": {"achieved": ach_m, "frac": ach_m / peak_f, "unit": "TFLOP/s",
+                              "flops_per_face": method_fpf,
+                              "note": "the plain method's FP64 op count per face / the same "
+                                      "time; above 1 because the certified filter takes most "
+                                      "decisions in FP32"},
+    }
 
 
 def beta_large_flops(w):
@@ -125,28 +229,6 @@ def flops_per_face_from_flags(flags_np, nd, H):
     tot_rec = sum(hist[s] * per[s] for s in range(5))
     nfaces = nrec / ((nd + 2) * 2)
     return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + tot_rec / nfaces, hist / nrec
-
-
-def value_flops(H, sel):
-    """FP64 flops of a reconstruction's value once its decisions are known:
-    the selected large stencil's linear scheme, or the fallback's three
-    3-point candidates and their weighted sum (weights tabulated)."""
-    return 2 * (2 * (sel + 2)) - 1 if sel else 21
-
-
-def executed_fp64_per_face(hist, exact_frac, nd, H):
-    """FP64 flops the face kernel executes per face when the certified
-    single-precision filter decides a fraction 1 - exact_frac of the
-    reconstructions: every reconstruction forms its 2H - 1 shifted values in
-    FP64; a decided one then evaluates only its value formula, an exact-path
-    one the whole method (both with the measured decision mix).  The
-    filter's own single-precision and integer work is not FP64."""
-    nrec = 2 * (nd + 2)
-    W = 2 * H
-    algo = sum(hist[s] * recon_flops(H, s) for s in range(5))
-    val = sum(hist[s] * value_flops(H, s) for s in range(5))
-    per_rec = (W - 1) + (1.0 - exact_frac) * val + exact_frac * algo
-    return flops_face_fixed(nd, H) + flops_per_cell_sweep(nd) + nrec * per_rec
 
 
 # ---------------------------------------------------------------------------
@@ -350,7 +432,9 @@ def run_batched(args, dev, stream):
         return e0.elapsed_time(e1) * 1e-3
 
     k_b = max(3, args.steps)
+    clocks = ClockSampler(dev.index)
     t_b = timed(T.TENO_BATCH_GRAPH, k_b, torch.from_numpy(U.copy()).to(dev))
+    clk = clocks.stop()
     t_p = timed(T.TENO_BATCH_PER_PROBLEM, 1, torch.from_numpy(U.copy()).to(dev))
     Ua = torch.from_numpy(U.copy()).to(dev)
     Ub = torch.from_numpy(U.copy()).to(dev)
@@ -360,6 +444,23 @@ def run_batched(args, dev, stream):
     same = bool(torch.equal(Ua, Ub))
     v_b = cells * k_b / t_b
     v_p = cells * 1 / t_p
+    # FP64 roofline of the step's face sweeps against the whole step's time
+    # (the kernels inside one CUDA graph are not timed apart); every
+    # reconstruction counted at its cheapest outcome, the largest stencil's
+    # value, so the figure is a lower bound of the work done
+    flops = instr = 0.0
+    for scheme in (8, 10):
+        H = scheme // 2
+        hist = [0.0] * 5
+        hist[H - 2] = 1.0
+        ti, _ = face_fp64_instructions(1, H, hist, 0.0, tf=tile, stored_prims=False)
+        nf = 3 * sum(c["n"][0] + 1 for c in cases if c["scheme"] == scheme)
+        flops += nf * (ti["dadd"] + ti["dmul"] + 2.0 * ti["dfma"])
+        instr += nf * (ti["dadd"] + ti["dmul"] + ti["dfma"])
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak_i = N_SM * FP64_LANES_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = flops / (t_b / k_b) / 1e12
+    achieved_i = instr / (t_b / k_b) / 1e9
     return {"workload": "%d independent 1D Riemann problems, N ~ U{64..4096} (%d cells), "
                         "TENO8|10 50/50, 10%% near vacuum with limiter, per-problem CFL 0.4"
                         % (len(probs), cells),
@@ -368,6 +469,17 @@ def run_batched(args, dev, stream):
             "speedup": v_b / v_p, "identical_states": same,
             "autotuned": {"tile_faces": tile, "warps_per_tile": tile // 32,
                           "blocks_per_sm": bps},
+            "clocks": clk,
+            "roofline": {"bound": "alu", "kernel": "batch_face_kernel (3 per step) + small "
+                                                  "kernels, one CUDA graph",
+                         "achieved": achieved_i, "peak": peak_i, "unit": "G FP64 instr/s",
+                         "frac": achieved_i / peak_i,
+                         "flops": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": achieved / peak},
+                         "counted": "FP64 instructions the three persistent face sweeps of a "
+                                    "step execute (largest-stencil value for every "
+                                    "reconstruction, primitives computed while staging), over "
+                                    "the whole step's time: a lower bound"},
             "mode": "persistent (problem, tile) work list, step captured in a CUDA graph"}
 
 
@@ -435,7 +547,7 @@ def run_adjoint(args, dev, stream):
 
     scale = U0.abs().amax(dim=1, keepdim=True)
     errs = []
-    for seed in (5003, 5004):
+    for seed in range(5003, 5003 + args.fd_directions):
         v = torch.from_numpy(workloads.smooth_field((4, n, n), seed).reshape(4, -1)).to(dev) * scale
         h = 1e-6
         fd = (frozen(U0 + h * v) - frozen(U0 - h * v)) / (2 * h)
@@ -447,8 +559,10 @@ def run_adjoint(args, dev, stream):
                         % (n, n, nsteps, every),
             "forward_s": t_f, "backward_s": t_b, "cost_ratio": t_b / t_f,
             "cost_ratio_excluding_recompute": (t_b - t_rec) / t_f,
-            "fd_frozen_decisions_max_rel_err": max(errs), "fd_directions": len(errs),
-            "loss": float(loss)}
+            "fd_frozen_decisions_max_rel_err": max(errs),
+            "fd_frozen_decisions_median_rel_err": float(sorted(errs)[len(errs) // 2]),
+            "fd_directions": len(errs),
+            "loss": float(loss.detach())}
 
 
 def run_noh(args, dev, stream, n=64, scheme=10, t_end=0.6):
@@ -482,6 +596,16 @@ def run_noh(args, dev, stream, n=64, scheme=10, t_end=0.6):
     torch.cuda.synchronize(dev)
     el = time.perf_counter() - t0
     nonphys = S.status()
+    # diagnostics of the final state from one right-hand side with the
+    # decision record: selections, C_T exponents, faces where the limiter bound
+    _, rec = S.rhs(U, dt, flags=True)
+    d0, d1, l0, _ = T.record_layout(p)
+    rec = rec.cpu().numpy()
+    _, hist = flops_per_face_from_flags(rec[:d1], 3, scheme // 2)
+    diag = {"selection_mix": selection_mix(hist, scheme),
+            "ct_exponent_mix": ct_exponent_hist(rec[:d1]),
+            "limiter_faces_frac": float(rec[l0:].mean())}
+    S.status()
     L = c["L"]
     dx = L / n
     cc = (np.arange(n) + 0.5) * dx
@@ -505,7 +629,17 @@ def run_noh(args, dev, stream, n=64, scheme=10, t_end=0.6):
             "nonphysical": nonphys, "shock_radius": r40, "shock_radius_exact": R,
             "pre_shock_shell_err_max": float((np.abs(prof[pre] - ex[pre]) / ex[pre]).max()),
             "post_shock_mean_density": float(prof[post].mean()), "post_shock_exact": 64.0,
-            "pre_shock_cell_scatter_p99": float(np.percentile(np.abs(rho[cell_pre] - exc) / exc, 99))}
+            "pre_shock_cell_scatter_p99": float(np.percentile(np.abs(rho[cell_pre] - exc) / exc, 99)),
+            "final_state_decisions": diag}
+
+
+def ct_exponent_hist(flags_np):
+    """Fractions of reconstructions per C_T exponent [beta] = 7 .. 14 (bits
+    5-7 of each decision byte hold [beta] - 7)."""
+    import numpy as np
+    h = np.bincount((flags_np >> 5).astype(np.int64), minlength=8).astype(np.float64)
+    h /= max(1, flags_np.size)
+    return {str(7 + k): float(h[k]) for k in range(8)}
 
 
 def selection_mix(hist, scheme):
@@ -516,9 +650,10 @@ def selection_mix(hist, scheme):
 
 
 def run_scheme_leg(args, dev, stream, scheme, n=256, steps=3):
-    """The same 256^3 workload with another scheme width (the twelve-point
-    TENO12-AA): time per step, rate and the face kernel's FP64 roofline
-    fraction (executed flops per face / live average launch time)."""
+    """The same 256^3 workload with another scheme width (the eight-point
+    TENO8-AA of the 3D configuration, the twelve-point TENO12-AA): time per
+    step, rate and the face kernel's FP64 roofline fraction (executed flops
+    per face / live average launch time)."""
     import torch
 
     import paper_2109_14340_gb300 as T
@@ -537,8 +672,9 @@ def run_scheme_leg(args, dev, stream, scheme, n=256, steps=3):
         step()
     torch.cuda.synchronize(dev)
     _, flags = solver.rhs(U, flags=True)
-    fl_np = flags.cpu().numpy()[:flags.numel() // 12 * 10]
+    fl_np = flags.cpu().numpy()[:T.record_layout(p)[1]]      # decision bytes
     fpf, hist = flops_per_face_from_flags(fl_np, 3, scheme // 2)
+    ct_hist = ct_exponent_hist(fl_np)
     del flags, fl_np
     clocks = ClockSampler(dev.index)
     T.teno_profile_enable(True)
@@ -558,25 +694,28 @@ def run_scheme_leg(args, dev, stream, scheme, n=256, steps=3):
     avg_launch_s = face_ms * 1e-3 / max(face_launches, 1)
     faces_per_launch = face_faces / max(face_launches, 1)
     exact_frac = face_exact / max(face_faces * 2 * 5, 1)
-    fpf_exec = executed_fp64_per_face(hist, exact_frac, 3, scheme // 2)
-    achieved = fpf_exec * faces_per_launch / avg_launch_s / 1e12
-    method_equiv = fpf * faces_per_launch / avg_launch_s / 1e12
     traffic_pf = read_traffic_per_face(scheme)
+    roof = fp64_roofline(hist, exact_frac, 3, scheme // 2, faces_per_launch, avg_launch_s, fpf)
+    roof.update({"exact_path_fraction": exact_frac, "avg_launch_ms": avg_launch_s * 1e3,
+                 "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
+                 "face_kernel_share": face_ms / ms if ms > 0 else None,
+                 "selection_mix": selection_mix(hist, scheme), "ct_exponent_mix": ct_hist})
     return {
         "workload": "the same 256^3 Taylor-Green + k^-5/3 field with TENO%d-AA, LLF, CFL 0.4"
                     % scheme,
         "steps": steps, "ms_per_step": ms / steps, "value": n ** 3 / (ms / steps * 1e-3),
-        "unit": UNIT, "nonphysical": solver.status(), "clocks": clk,
-        "roofline": {"bound": "alu", "kernel": "face_kernel (x/y/z face sweeps)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "fp64_flops_per_face": fpf_exec,
-                     "exact_path_fraction": exact_frac,
-                     "method_equivalent": {"achieved": method_equiv, "frac": method_equiv / peak},
-                     "avg_launch_ms": avg_launch_s * 1e3,
-                     "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
-                     "face_kernel_share": face_ms / ms if ms > 0 else None,
-                     "selection_mix": selection_mix(hist, scheme)},
+        "unit": UNIT, "nonphysical": solver.status(), "clocks": clk, "roofline": roof,
     }
+
+
+def measured_hbm_peak():
+    """HBM copy bandwidth from MEASURED_PEAKS.json (measured on this machine's
+    GB300s), else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def read_traffic_per_face(scheme):
@@ -630,8 +769,9 @@ def run_ours(args, rank, world, local_rank):
 
     # decision histogram of the current state (untimed) -> algorithmic flops
     _, flags = solver.rhs(U, flags=True)
-    fl_np = flags.cpu().numpy()[:flags.numel() // 12 * 10]   # decision bytes only
+    fl_np = flags.cpu().numpy()[:T.record_layout(p)[1]]      # decision bytes only
     fpf, hist = flops_per_face_from_flags(fl_np, 3, scheme // 2)
+    ct_hist = ct_exponent_hist(fl_np)
     del flags, fl_np
 
     clocks = ClockSampler(local_rank)
@@ -723,11 +863,16 @@ def run_ours(args, rank, world, local_rank):
     avg_launch_s = face_ms * 1e-3 / max(face_launches, 1)
     faces_per_launch = face_faces / max(face_launches, 1)
     exact_frac = face_exact / max(face_faces * 2 * 5, 1)
-    fpf_exec = executed_fp64_per_face(hist, exact_frac, 3, scheme // 2)
-    achieved = fpf_exec * faces_per_launch / avg_launch_s / 1e12
-    method_equiv = fpf * faces_per_launch / avg_launch_s / 1e12
     traffic_pf = read_traffic_per_face(scheme)
-    launches_per_step = 2 + 3 * (2 + 3)
+    roof = fp64_roofline(hist, exact_frac, 3, scheme // 2, faces_per_launch, avg_launch_s, fpf)
+    roof.update({"peak_probe_measured_tflops": probe,
+                 "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
+                 "exact_path_fraction": exact_frac, "faces_per_launch": faces_per_launch,
+                 "avg_launch_ms": avg_launch_s * 1e3,
+                 "face_kernel_share": face_ms / ms if ms > 0 else None,
+                 "selection_mix": selection_mix(hist, scheme), "ct_exponent_mix": ct_hist})
+    launches_per_step = 3 + 3 * (2 + 3)       # CFL (2), primitives; per stage prepare, 3 sweeps, combine
+    hbm_peak, hbm_src = measured_hbm_peak()
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, stream)
@@ -740,6 +885,9 @@ def run_ours(args, rank, world, local_rank):
     teno12 = None
     if not args.no_teno12 and scheme != 12:
         teno12 = run_scheme_leg(args, dev, stream, 12, n=n)
+    teno8 = None
+    if not args.no_teno8 and scheme != 8:
+        teno8 = run_scheme_leg(args, dev, stream, 8, n=n)
 
     if rank != 0:
         if dist is not None:
@@ -760,29 +908,12 @@ def run_ours(args, rank, world, local_rank):
             "workload": workload_desc(n, scheme),
             "scheme": scheme, "cells": cells, "parallelism": "independent problem per GPU",
             "l2": "state 671 MB > 129 MB L2 (no flush needed)"},
-        "roofline": {
-            "bound": "alu", "kernel": "face_kernel (x/y/z face sweeps)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "peak_probe_measured": probe,
-            "traffic": (traffic_pf * faces_per_launch) if traffic_pf else None,
-            "counted": "FP64 flops executed per face (add/sub/mul/div/sqrt 1, fma 2) from the "
-                       "method's op count, with the live fraction of reconstructions that took "
-                       "the exact FP64 path",
-            "fp64_flops_per_face": fpf_exec, "exact_path_fraction": exact_frac,
-            "method_equivalent": {
-                "achieved": method_equiv, "frac": method_equiv / peak,
-                "flops_per_face": fpf,
-                "note": "the plain method's FP64 op count per face / the same time; above 1 "
-                        "because the certified filter takes most decisions in FP32"},
-            "faces_per_launch": faces_per_launch,
-            "avg_launch_ms": avg_launch_s * 1e3,
-            "face_kernel_share": face_ms / ms if ms > 0 else None,
-            "selection_mix": selection_mix(hist, scheme)},
+        "roofline": roof,
         "roofline_hbm": {
             "bound": "hbm", "achieved": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9,
-            "peak": 6782.1, "unit": "GB/s",
-            "frac": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9 / 6782.1,
+            "peak": hbm_peak, "unit": "GB/s",
+            "frac": value * HBM_BYTES_PER_CELL_UPDATE_3D / 1e9 / hbm_peak,
+            "peak_source": hbm_src,
             "note": "algorithmic 320 B per cell-update; the path is FP64-ALU bound"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes + 8,
@@ -797,6 +928,7 @@ def run_ours(args, rank, world, local_rank):
         "adjoint": adjoint,
         "noh": noh,
         "teno12": teno12,
+        "teno8": teno8,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -61,6 +61,19 @@ extern "C" {
                                   ghost -r primitives = 2 phi' - those of cell
                                   r-1 (second order); not differentiated by
                                   the adjoint calls, not in batched mode      */
+#define TENO_BC_HALO 5         /* domain decomposition: the H ghost cells of
+                                  the side are a neighbouring sub-domain's
+                                  cells, given in a caller-owned halo array
+                                  (bc_state_lo / bc_state_hi) of conserved
+                                  variables [ncons][H][m]: plane q holds cell
+                                  -H + q below the sub-domain (low side) or
+                                  n + q above it (high side), m = cells of a
+                                  plane in the order of the two other axes, x
+                                  fastest; the caller fills it before each
+                                  evaluation (teno_rk3_stage).  Not with the
+                                  limiter in 2D / 3D (its direction weights
+                                  need the whole domain's wave speeds), not in
+                                  the adjoint calls or batched mode           */
 
 /* Flux splitting of the characteristic fluxes (Sec. 5). */
 #define TENO_SPLIT_LLF 0       /* per field k: alpha_k = max |lambda_k| over
@@ -102,7 +115,8 @@ typedef struct teno_params {
      * major, then the boundary faces in the order of the two other axes,
      * x fastest: state[q * m + s], m = product of n over the axes != d,
      * s = the face's index among them (d = 0: y + n[1] z; d = 1: x + n[0] z;
-     * d = 2: x + n[0] y). */
+     * d = 2: x + n[0] y).  TENO_BC_HALO sides take their halo array here
+     * (layout at TENO_BC_HALO). */
     const double *bc_state_lo[3];
     const double *bc_state_hi[3];
 } teno_params;
@@ -128,7 +142,10 @@ int teno_workspace_bytes(const teno_params *p, size_t *bytes);
  * (mod 8).  Part 2, for each direction in turn, for each face, one
  * little-endian 16-bit word: the stencil cells (0 .. 2H-1, from cell i-H+1)
  * where the splitting speeds are maximal (first maximum), 4 bits each for
- * |u_d - c|, |u_d|, |u_d + c| and |u_d| + c. */
+ * |u_d - c|, |u_d|, |u_d + c| and |u_d| + c.  Part 3, for each direction in
+ * turn, for each face, one byte: 1 where the positivity-preserving limiter
+ * (Sec. 5.3) bound, i.e. blended the face flux toward the Lax-Friedrichs
+ * flux, else 0 (always 0 with p->limiter == 0). */
 int teno_flags_bytes(const teno_params *p, size_t *bytes);
 
 /* Semi-discrete right-hand side L(U) = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d
@@ -277,6 +294,42 @@ int teno_rk3_step_frozen(const teno_params *p, double *U, double dt, const uint8
 int teno_rk3_step_vjp(const teno_params *p, const double *Un, const double *U1, const double *U2,
                       const uint8_t *flags, double dt, double *abar, void *ws, size_t ws_bytes,
                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition (sub-domains exchanging halo planes).  A grid split
+ * into slabs along an axis is advanced slab by slab: each slab is a
+ * teno_params with TENO_BC_HALO on its inner sides, and the caller fills the
+ * halo arrays from the neighbouring slabs' states before every evaluation
+ * (a device copy on one GPU; a send / receive between GPUs).  Each slab
+ * computes its boundary faces from the same stencil cells as the undivided
+ * grid, so the slabs' states equal the undivided grid's bit for bit.
+ * ------------------------------------------------------------------------ */
+
+/* One stage of the SSP-RK3 step (Eq. Runge-kutta) of teno_rk3_step, so that
+ * halos can be exchanged between stages: stage 1 reads U and writes
+ * Us = U + dt L(U); stage 2 overwrites Us with 3/4 U + 1/4 (Us + dt L(Us));
+ * stage 3 writes U = 1/3 U + 2/3 (Us + dt L(Us)).  The stage input (U, then
+ * Us) is the state whose halo the caller provides.  Us: device, ncons *
+ * ncells doubles, caller-owned, not aliasing U.  dt from dt_device when not
+ * NULL, else the host dt.  The workspace carries the primitives of each
+ * stage's output into the next stage: call stages 1, 2, 3 in order on the
+ * same U, Us and ws, changing neither U nor Us in between (the halo arrays
+ * may change).  The three stages give bitwise teno_rk3_step. */
+int teno_rk3_stage(const teno_params *p, int stage, double *U, double *Us, double dt,
+                   const double *dt_device, void *ws, size_t ws_bytes, void *stream);
+
+/* The wave-speed maxima A_d = max over the interior cells of (|u_d| + c),
+ * d < ndim, written as doubles to amax_device[0 .. ndim-1] (device memory,
+ * 8-byte aligned): the per-sub-domain part of teno_cfl_dt. */
+int teno_wave_speeds(const teno_params *p, const double *U, double *amax_device, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* dt = cfl / sum_d (A_d / dx_d) with A_d the largest of ncopies rows of
+ * maxima amax_device[k * 3 + d] (k < ncopies, d < ndim; e.g. one row per
+ * sub-domain, or one row already reduced across GPUs), written to the device
+ * scalar *dt_device; bitwise the dt teno_cfl_dt gives for the whole grid. */
+int teno_dt_from_speeds(const teno_params *p, const double *amax_device, int32_t ncopies,
+                        double cfl, double *dt_device, void *stream);
 
 /* Size of the device array behind teno_rhs_static: 16 MiB. */
 #define TENO_RHS_STATIC_SCRATCH_BYTES (16u << 20)

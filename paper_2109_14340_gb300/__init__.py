@@ -19,7 +19,7 @@ from . import _build
 
 TENO_OK, TENO_EINVAL, TENO_ECUDA, TENO_ENONPHYSICAL, TENO_ETIMEOUT = 0, 1, 2, 3, 4
 TENO_BC_PERIODIC, TENO_BC_TRANSMISSIVE, TENO_BC_SLIPWALL = 0, 1, 2
-TENO_BC_NOSLIP, TENO_BC_DIRICHLET = 3, 4
+TENO_BC_NOSLIP, TENO_BC_DIRICHLET, TENO_BC_HALO = 3, 4, 5
 TENO_SPLIT_LLF, TENO_SPLIT_RUSANOV = 0, 1
 
 _lock = threading.Lock()
@@ -85,6 +85,9 @@ def load():
         lib.teno_advance_host.argtypes = [P, vp, vp, ctypes.c_int, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double), vp, sz, vp]
         lib.teno_rhs_static.argtypes = [P, vp, vp, ctypes.c_double, vp, vp]
+        lib.teno_rk3_stage.argtypes = [P, ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, sz, vp]
+        lib.teno_wave_speeds.argtypes = [P, vp, vp, vp, sz, vp]
+        lib.teno_dt_from_speeds.argtypes = [P, vp, ctypes.c_int32, ctypes.c_double, vp, vp]
         u8p = ctypes.c_void_p
         lib.teno_adjoint_workspace_bytes.argtypes = [P, ctypes.POINTER(sz)]
         lib.teno_rhs_vjp.argtypes = [P, vp, vp, vp, vp, vp, sz, vp]
@@ -117,7 +120,8 @@ def load():
                      "teno_batch_workspace_bytes", "teno_batch_autotune", "teno_batch_rk3_steps",
                      "teno_batch_times", "teno_adjoint_workspace_bytes", "teno_rhs_vjp",
                      "teno_rk3_step_record", "teno_rk3_step_vjp", "teno_rhs_frozen",
-                     "teno_rk3_step_frozen"):
+                     "teno_rk3_step_frozen", "teno_rk3_stage", "teno_wave_speeds",
+                     "teno_dt_from_speeds"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -130,7 +134,8 @@ EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno
            "teno_batch_create", "teno_batch_workspace_bytes", "teno_batch_autotune",
            "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy",
            "teno_adjoint_workspace_bytes", "teno_rhs_vjp", "teno_rk3_step_record",
-           "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen")
+           "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen",
+           "teno_rk3_stage", "teno_wave_speeds", "teno_dt_from_speeds")
 
 TENO_RHS_STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -207,6 +212,19 @@ def teno_flags_bytes(p: teno_params) -> int:
     return n.value
 
 
+def record_layout(p: teno_params):
+    """Byte offsets of the three parts of a decision record (include/teno.h,
+    teno_flags_bytes): (decision bytes, argmax words, limiter bytes, total)."""
+    nc = p.ndim + 2
+    faces = 0
+    for d in range(p.ndim):
+        m = 1
+        for a in range(3):
+            m *= p.n[a] + (1 if a == d else 0)
+        faces += m
+    return 0, faces * nc * 2, faces * nc * 2 + 2 * faces, faces * (nc * 2 + 3)
+
+
 def teno_rhs(p, U, rhs, dt_limiter=0.0, flags=None, ws=None, stream=None):
     _check(load().teno_rhs(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter), _ptr(flags),
                            _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "teno_rhs")
@@ -231,6 +249,24 @@ def teno_rhs_static(p, U, rhs, dt_limiter=0.0, flags=None, stream=None):
 def teno_rk3_step(p, U, dt=0.0, dt_device=None, ws=None, stream=None):
     _check(load().teno_rk3_step(ctypes.byref(p), _ptr(U), float(dt), _ptr(dt_device), _ptr(ws),
                                 ws.numel() * ws.element_size(), _stream(stream)), "teno_rk3_step")
+
+
+def teno_rk3_stage(p, stage, U, Us, dt=0.0, dt_device=None, ws=None, stream=None):
+    _check(load().teno_rk3_stage(ctypes.byref(p), int(stage), _ptr(U), _ptr(Us), float(dt),
+                                 _ptr(dt_device), _ptr(ws), ws.numel() * ws.element_size(),
+                                 _stream(stream)), "teno_rk3_stage")
+
+
+def teno_wave_speeds(p, U, amax_device, ws, stream=None):
+    _check(load().teno_wave_speeds(ctypes.byref(p), _ptr(U), _ptr(amax_device), _ptr(ws),
+                                   ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_wave_speeds")
+
+
+def teno_dt_from_speeds(p, amax_device, ncopies, cfl, dt_device, stream=None):
+    _check(load().teno_dt_from_speeds(ctypes.byref(p), _ptr(amax_device), int(ncopies),
+                                      float(cfl), _ptr(dt_device), _stream(stream)),
+           "teno_dt_from_speeds")
 
 
 def teno_cfl_dt(p, U, cfl, dt_device, ws=None, stream=None):
@@ -324,6 +360,139 @@ class Solver:
 
     def status(self, stream=None):
         return teno_status(self.ws, stream)
+
+
+# ---------------------------------------------------------------------------
+# domain decomposition: slabs along the slowest axis exchanging halo planes
+# ---------------------------------------------------------------------------
+
+def slab_plan(n_axis, parts, H, periodic):
+    """Split n_axis cells into `parts` slabs (sizes differ by at most one).
+    Returns per slab (start, stop, lo, hi): lo / hi the neighbouring slab
+    whose cells fill the halo on that side, or None at a physical end.
+    Every slab needs at least H cells, so its halo comes from one neighbour."""
+    if parts < 1 or n_axis < parts * H:
+        raise ValueError("cannot split %d cells into %d slabs of at least %d" % (n_axis, parts, H))
+    base, extra = divmod(n_axis, parts)
+    plan, start = [], 0
+    for k in range(parts):
+        size = base + (1 if k < extra else 0)
+        lo = k - 1 if k > 0 else (parts - 1 if periodic else None)
+        hi = k + 1 if k < parts - 1 else (0 if periodic else None)
+        plan.append((start, start + size, lo, hi))
+        start += size
+    return plan
+
+
+def halo_planes(U, n_slab, m, H, side):
+    """The H boundary planes of a slab state U ([nc][n_slab * m], the slab
+    axis slowest) that a neighbour needs: its first H planes ('lo') or its
+    last H planes ('hi'), as a [nc][H * m] view."""
+    V = U.view(U.shape[0], n_slab * m)
+    return V[:, :H * m] if side == "lo" else V[:, (n_slab - H) * m:]
+
+
+def exchange_halos_dist(U, n_slab, m, H, halo_lo, halo_hi, lo, hi, group=None):
+    """Halo exchange of one slab with its neighbouring ranks through
+    torch.distributed (any backend; the tests run gloo with host tensors):
+    send the first / last H planes to the lo / hi neighbour, receive the
+    neighbours' planes into halo_lo / halo_hi ([nc][H * m], contiguous).
+    lo / hi: neighbour ranks or None at a physical end."""
+    import torch.distributed as dist
+    reqs = []
+    if lo is not None:
+        reqs.append(dist.isend(halo_planes(U, n_slab, m, H, "lo").contiguous(), lo, group, tag=1))
+        reqs.append(dist.irecv(halo_lo, lo, group, tag=2))
+    if hi is not None:
+        reqs.append(dist.isend(halo_planes(U, n_slab, m, H, "hi").contiguous(), hi, group, tag=2))
+        reqs.append(dist.irecv(halo_hi, hi, group, tag=1))
+    for r in reqs:
+        r.wait()
+
+
+class SlabDecomposition:
+    """A grid split into slabs along its slowest axis, every slab a
+    sub-problem on this device with TENO_BC_HALO on its inner sides; the
+    halo planes are copied between slabs on the device before every stage
+    and the CFL time step is taken over all slabs, so the slabs advance
+    exactly like the undivided grid (bitwise).  The halo copies are where a
+    multi-GPU run would exchange planes between ranks (exchange_halos_dist)."""
+
+    def __init__(self, p: teno_params, parts: int, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        nd = p.ndim
+        ax = nd - 1
+        self.ax, self.nc, self.H = ax, nd + 2, p.scheme // 2
+        self.m = 1
+        for a in range(ax):
+            self.m *= p.n[a]
+        periodic = p.bc_lo[ax] == TENO_BC_PERIODIC
+        self.plan = slab_plan(p.n[ax], parts, self.H, periodic)
+        self.params, self.halos, self.solvers, self.Us = [], [], [], []
+        for (a0, a1, lo, hi) in self.plan:
+            hl = torch.zeros(self.nc, self.H * self.m, dtype=torch.float64, device=self.device)
+            hh = torch.zeros_like(hl)
+            q = teno_params()
+            ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(p))
+            q.n[ax] = a1 - a0
+            if lo is not None:
+                q.bc_lo[ax] = TENO_BC_HALO
+                q.bc_state_lo[ax] = hl.data_ptr()
+            if hi is not None:
+                q.bc_hi[ax] = TENO_BC_HALO
+                q.bc_state_hi[ax] = hh.data_ptr()
+            self.params.append(q)
+            self.halos.append((hl, hh))
+            self.solvers.append(Solver(q, self.device))
+            self.Us.append(None)
+        self.amax = torch.zeros(len(self.plan) * 3, dtype=torch.float64, device=self.device)
+        self.dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+
+    def split(self, U):
+        """Slab states (copies) of a whole-grid state [nc][cells]."""
+        V = U.view(self.nc, -1)
+        return [V[:, a0 * self.m:a1 * self.m].contiguous() for (a0, a1, _, _) in self.plan]
+
+    def join(self, parts):
+        import torch
+        return torch.cat(parts, dim=1)
+
+    def exchange(self, states):
+        """Fill every slab's halo arrays from its neighbours' current states."""
+        for k, (a0, a1, lo, hi) in enumerate(self.plan):
+            hl, hh = self.halos[k]
+            if lo is not None:
+                n_lo = self.plan[lo][1] - self.plan[lo][0]
+                hl.copy_(halo_planes(states[lo], n_lo, self.m, self.H, "hi"))
+            if hi is not None:
+                n_hi = self.plan[hi][1] - self.plan[hi][0]
+                hh.copy_(halo_planes(states[hi], n_hi, self.m, self.H, "lo"))
+
+    def cfl_dt(self, parts, cfl=0.4):
+        """The whole grid's CFL time step from every slab's wave speeds."""
+        for k, U in enumerate(parts):
+            teno_wave_speeds(self.params[k], U, self.amax[3 * k:3 * k + 3], self.solvers[k].ws)
+        teno_dt_from_speeds(self.params[0], self.amax, len(parts), cfl, self.dt)
+        return self.dt
+
+    def step(self, parts, dt=None):
+        """One SSP-RK3 step of every slab, halos exchanged before each stage;
+        dt=None uses the device scalar of cfl_dt."""
+        import torch
+        for k, U in enumerate(parts):
+            if self.Us[k] is None or self.Us[k].shape != U.shape:
+                self.Us[k] = torch.empty_like(U)
+        for stage in (1, 2, 3):
+            self.exchange(parts if stage == 1 else self.Us)
+            for k, U in enumerate(parts):
+                s = self.solvers[k]
+                teno_rk3_stage(self.params[k], stage, U, self.Us[k],
+                               0.0 if dt is None else float(dt),
+                               self.dt if dt is None else None, s.ws)
+
+    def status(self):
+        return sum(s.status() for s in self.solvers)
 
 
 # ---------------------------------------------------------------------------
@@ -472,8 +641,9 @@ def _rollout_class():
     class TenoRollout(torch.autograd.Function):
         """nsteps SSP-RK3 steps at a fixed dt; the backward walks checkpoint
         segments in reverse: recompute the segment's steps keeping stage
-        states and decision records, then apply teno_rk3_step_vjp step by
-        step (decisions frozen as in the forward)."""
+        states and decision records (the last segment's are kept from the
+        forward), then apply teno_rk3_step_vjp step by step (decisions frozen
+        as in the forward)."""
 
         @staticmethod
         def forward(ctx, U0, p, dt, nsteps, every):
@@ -481,12 +651,25 @@ def _rollout_class():
             ws = aligned_workspace(teno_workspace_bytes(p), dev)
             U = U0.detach().contiguous().clone()
             ckpts = []
+            # the last segment is recorded as it is computed (stage states and
+            # decision records, bitwise the same steps): the backward starts
+            # with it and need not recompute it
+            last = ((nsteps - 1) // every) * every if nsteps > 0 else 0
+            flb = teno_flags_bytes(p)
+            rec = []
             for k in range(nsteps):
                 if k % every == 0:
                     ckpts.append(U.clone())
-                teno_rk3_step(p, U, float(dt), None, ws)
+                if k >= last:
+                    Un, U1, U2 = U.clone(), torch.empty_like(U), torch.empty_like(U)
+                    fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
+                    teno_rk3_step_record(p, U, float(dt), U1, U2, fl, ws)
+                    rec.append((Un, U1, U2, fl))
+                else:
+                    teno_rk3_step(p, U, float(dt), None, ws)
             ctx.p, ctx.dt, ctx.nsteps, ctx.every = p, float(dt), nsteps, every
             ctx.ckpts = ckpts
+            ctx.last_rec = rec
             return U
 
         @staticmethod
@@ -501,19 +684,23 @@ def _rollout_class():
             for s in reversed(range(nseg)):
                 start = s * every
                 stop = min(start + every, nsteps)
-                U = ctx.ckpts[s].clone()
-                rec = []
-                for _ in range(start, stop):
-                    Un = U.clone()
-                    U1 = torch.empty_like(U)
-                    U2 = torch.empty_like(U)
-                    fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
-                    teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
-                    rec.append((Un, U1, U2, fl))
+                if s == nseg - 1 and ctx.last_rec:
+                    rec, ctx.last_rec = ctx.last_rec, None
+                else:
+                    U = ctx.ckpts[s].clone()
+                    rec = []
+                    for _ in range(start, stop):
+                        Un = U.clone()
+                        U1 = torch.empty_like(U)
+                        U2 = torch.empty_like(U)
+                        fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
+                        teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
+                        rec.append((Un, U1, U2, fl))
                 for Un, U1, U2, fl in reversed(rec):
                     teno_rk3_step_vjp(p, Un, U1, U2, fl, dt, abar, aws)
                 del rec
             ctx.ckpts = None
+            ctx.last_rec = None
             return abar, None, None, None, None
 
     return TenoRollout

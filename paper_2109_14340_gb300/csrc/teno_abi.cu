@@ -7,11 +7,21 @@
 #include <mutex>
 
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "teno.h"
 #include "teno_face.cuh"
 
 namespace teno {
+
+// NVTX range around the enqueueing of one phase (visible to Nsight tools;
+// a no-op when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Explicit instantiations live in teno_face8.cu / teno_face10.cu.
 cudaError_t launch_face8(int nd, int d, const FaceArgs &a, cudaStream_t s);
@@ -180,6 +190,23 @@ __global__ void cfl_finalize_kernel(Status *st, int nd, double cfl, double3 inv_
     if (accumulate) st->t_accum = st->t_accum + dt;
 }
 
+// dt = cfl / sum_d A_d / dx_d with A_d the largest of ncopies rows of maxima
+// (sub-domains): the arithmetic of cfl_finalize_kernel on the combined maxima.
+__global__ void dt_from_speeds_kernel(const double *amax, int ncopies, int nd, double cfl,
+                                      double3 inv_dx, double *dt_out)
+{
+    const double idx[3] = {inv_dx.x, inv_dx.y, inv_dx.z};
+    double A[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < ncopies; k++)
+        for (int d = 0; d < nd; d++) {
+            const double v = amax[k * 3 + d];
+            if (v > A[d]) A[d] = v;
+        }
+    double S = A[0] * idx[0];
+    for (int d = 1; d < nd; d++) S = S + A[d] * idx[d];
+    *dt_out = cfl / S;
+}
+
 // Stage preparation: dt from the host value or a device scalar, and the
 // limiter's effective dt/dx per direction: dt/dx in 1D; (dt S) / A_d with
 // S = sum_d A_d/dx_d in several dimensions (each direction's one-sided
@@ -285,10 +312,14 @@ static int validate(const teno_params *p)
             for (int side = 0; side < 2; side++) {
                 const int b = side ? p->bc_hi[a] : p->bc_lo[a];
                 const double *st = side ? p->bc_state_hi[a] : p->bc_state_lo[a];
-                if (b < TENO_BC_PERIODIC || b > TENO_BC_DIRICHLET) return TENO_EINVAL;
-                // a state array exactly on the Dirichlet sides (16-byte aligned)
-                if ((b == TENO_BC_DIRICHLET) != (st != nullptr)) return TENO_EINVAL;
+                if (b < TENO_BC_PERIODIC || b > TENO_BC_HALO) return TENO_EINVAL;
+                // a state array exactly on the Dirichlet and halo sides (16-byte aligned)
+                if ((b == TENO_BC_DIRICHLET || b == TENO_BC_HALO) != (st != nullptr))
+                    return TENO_EINVAL;
                 if (st && ((uintptr_t)st & 15)) return TENO_EINVAL;
+                // the limiter's direction weights need the whole domain's wave
+                // speeds, which a sub-domain does not see
+                if (b == TENO_BC_HALO && p->limiter && p->ndim > 1) return TENO_EINVAL;
             }
             if ((p->bc_lo[a] == TENO_BC_PERIODIC) != (p->bc_hi[a] == TENO_BC_PERIODIC))
                 return TENO_EINVAL;
@@ -371,6 +402,7 @@ static cudaError_t launch_wave_max(const teno_params *p, const double *U, Status
 static cudaError_t launch_prims(const teno_params *p, const double *U, char *ws, cudaStream_t s,
                                 double **P_out)
 {
+    NvtxRange range("teno primitives");
     const Layout L = layout(p);
     Status *st = (Status *)(ws + L.status);
     double *P = (double *)(ws + L.prims);
@@ -417,6 +449,11 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
                  double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s,
                  const uint8_t *frozen, const double *P_in, double *P_out)
 {
+    static const char *kStageName[4] = {"teno rhs", "teno rk3 stage 1", "teno rk3 stage 2",
+                                        "teno rk3 stage 3"};
+    static const char *kSweepName[3] = {"teno face sweep x", "teno face sweep y",
+                                        "teno face sweep z"};
+    NvtxRange range(kStageName[mode]);
     const Layout L = layout(p);
     Status *st = (Status *)(ws + L.status);
     const Consts K = consts_of(p);
@@ -431,8 +468,11 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     // directions' maximising-cell words
     size_t dec_bytes = 0;
     for (int d = 0; d < nd; d++) dec_bytes += (size_t)face_grid(p, d) * nc * 2;
+    size_t nfaces_all = 0;
+    for (int d = 0; d < nd; d++) nfaces_all += (size_t)face_grid(p, d);
     uint16_t *am = flags ? (uint16_t *)(flags + dec_bytes) : nullptr;
     const uint16_t *fam = frozen ? (const uint16_t *)(frozen + dec_bytes) : nullptr;
+    uint8_t *lr = flags ? flags + dec_bytes + 2 * nfaces_all : nullptr;   // limiter bytes
     for (int d = 0; d < nd; d++) {
         FaceArgs a;
         a.U = Uk;
@@ -442,6 +482,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.frozen = fz;
         a.argmax = am;
         a.frozen_argmax = fam;
+        a.limrec = lr;
         a.st = st;
         for (int k = 0; k < 3; k++) a.n[k] = p->n[k];
         a.ncell = ncells(p);
@@ -463,14 +504,17 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
             g_prof.nf[slot] = a.nfaces - (a.skip_last ? a.ncell / p->n[d] : 0);   // faces computed
             CUDA_TRY(profile_mark(0, slot, s));
         }
+        nvtxRangePushA(kSweepName[d]);
         cudaError_t e = (p->scheme == 8) ? launch_face8(nd, d, a, s)
                       : (p->scheme == 10 ? launch_face10(nd, d, a, s) : launch_face12(nd, d, a, s));
+        nvtxRangePop();
         if (e != cudaSuccess) return TENO_ECUDA;
         if (slot >= 0) CUDA_TRY(profile_mark(1, slot, s));
         if (fl) fl += (size_t)face_grid(p, d) * nc * 2;
         if (fz) fz += (size_t)face_grid(p, d) * nc * 2;
         if (am) am += face_grid(p, d);
         if (fam) fam += face_grid(p, d);
+        if (lr) lr += face_grid(p, d);
     }
     CombineArgs c;
     for (int d = 0; d < 3; d++) {
@@ -492,6 +536,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
     c.K = K;
     const int blk = 256;
     const dim3 grd((unsigned)((p->n[0] + blk - 1) / blk), (unsigned)p->n[1], (unsigned)p->n[2]);
+    NvtxRange crange("teno combine");
     if (nd == 1) combine_kernel<1><<<grd, blk, 0, s>>>(c);
     else if (nd == 2) combine_kernel<2><<<grd, blk, 0, s>>>(c);
     else combine_kernel<3><<<grd, blk, 0, s>>>(c);
@@ -540,7 +585,7 @@ int teno_flags_bytes(const teno_params *p, size_t *bytes)
     if (r) return r;
     if (!bytes) return TENO_EINVAL;
     size_t t = 0;
-    for (int d = 0; d < p->ndim; d++) t += (size_t)face_grid(p, d) * (ncons(p) * 2 + 2);
+    for (int d = 0; d < p->ndim; d++) t += (size_t)face_grid(p, d) * (ncons(p) * 2 + 2 + 1);
     *bytes = t;
     return TENO_OK;
 }
@@ -643,8 +688,62 @@ int teno_cfl_dt(const teno_params *p, const double *U, double cfl, double *dt_de
     if (ws_bytes < layout(p).total || !(cfl > 0.0)) return TENO_EINVAL;
     Status *st = (Status *)((char *)ws + layout(p).status);
     cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange range("teno cfl dt");
     CUDA_TRY(launch_wave_max(p, U, st, 0, s));
     cfl_finalize_kernel<<<1, 1, 0, s>>>(st, p->ndim, cfl, inv_dx_of(p), dt_device, 0);
+    CUDA_TRY(cudaGetLastError());
+    return TENO_OK;
+}
+
+int teno_rk3_stage(const teno_params *p, int stage_k, double *U, double *Us, double dt,
+                   const double *dt_device, void *ws, size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(Us) || check_ptr(ws) || U == Us || ((uintptr_t)dt_device & 7))
+        return TENO_EINVAL;
+    if (stage_k < 1 || stage_k > 3 || ws_bytes < layout(p).total) return TENO_EINVAL;
+    if (!dt_device && !(dt >= 0.0)) return TENO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *P = (double *)((char *)ws + layout(p).prims);
+    // the stages of teno_rk3_step, the primitives carried in the workspace
+    if (stage_k == 1) {
+        CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
+        return stage(p, U, U, Us, 1, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, P);
+    }
+    if (stage_k == 2)
+        return stage(p, Us, U, Us, 2, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, P);
+    return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, nullptr);
+}
+
+int teno_wave_speeds(const teno_params *p, const double *U, double *amax_device, void *ws,
+                     size_t ws_bytes, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (check_ptr(U) || check_ptr(ws) || !amax_device || ((uintptr_t)amax_device & 7))
+        return TENO_EINVAL;
+    if (ws_bytes < layout(p).total) return TENO_EINVAL;
+    Status *st = (Status *)((char *)ws + layout(p).status);
+    cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange range("teno wave speeds");
+    CUDA_TRY(launch_wave_max(p, U, st, 0, s));
+    // the maxima are kept as the bit patterns of non-negative doubles
+    CUDA_TRY(cudaMemcpyAsync(amax_device, st->amax, sizeof(double) * p->ndim,
+                             cudaMemcpyDeviceToDevice, s));
+    return TENO_OK;
+}
+
+int teno_dt_from_speeds(const teno_params *p, const double *amax_device, int32_t ncopies,
+                        double cfl, double *dt_device, void *stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (!amax_device || ((uintptr_t)amax_device & 7) || !dt_device || ((uintptr_t)dt_device & 7))
+        return TENO_EINVAL;
+    if (ncopies < 1 || !(cfl > 0.0)) return TENO_EINVAL;
+    dt_from_speeds_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(amax_device, ncopies, p->ndim, cfl,
+                                                             inv_dx_of(p), dt_device);
     CUDA_TRY(cudaGetLastError());
     return TENO_OK;
 }

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         const int64_t pg = ps + p;
         if (pg >= npen) continue;
         int rule;                      // 0 copy, 1 slip-wall / 2 no-slip mirror
-        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, rule);
+        const int64_t gi = map_index(f0 - H + j, nD, H, a.bc_lo, a.bc_hi, rule);
         int64_t id;
         if (D == 0) id = gi + n0 * (pg + n1 * z);
         else if (D == 1) id = pg + n0 * (gi + n1 * z);
@@ -773,7 +773,7 @@ int check_adj(const teno_params *p, void *ws, size_t ws_bytes)
     if (r) return r;
     if (p->limiter) return TENO_EINVAL;
     for (int d = 0; d < p->ndim; d++)
-        if (p->bc_lo[d] == TENO_BC_DIRICHLET || p->bc_hi[d] == TENO_BC_DIRICHLET) return TENO_EINVAL;
+        if (p->bc_lo[d] >= TENO_BC_DIRICHLET || p->bc_hi[d] >= TENO_BC_DIRICHLET) return TENO_EINVAL;
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < adj_layout(p).total) return TENO_EINVAL;
     return TENO_OK;
 }

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         a.frozen = nullptr;
         a.argmax = nullptr;
         a.frozen_argmax = nullptr;
+        a.limrec = nullptr;
         a.st = st;
         a.n[0] = d.n; a.n[1] = 1; a.n[2] = 1;
         a.ncell = d.n;

@@ -27,11 +27,13 @@ struct FaceArgs {
     uint16_t *argmax;      // per face: the maximising stencil cells of the splitting
                            // speeds (4 bits each: u-c, u, u+c, |u|+c), or nullptr
     const uint16_t *frozen_argmax;   // recorded maximising cells to apply, or nullptr
+    uint8_t *limrec;       // per face: 1 where the positivity limiter bound, or nullptr
     Status *st;
     int64_t n[3];
     int64_t ncell, nfaces;
     int bc_lo, bc_hi;      // boundary rules at the two ends of axis D
-    const double *bcs_lo, *bcs_hi;   // Dirichlet boundary-face states of axis D, or nullptr
+    const double *bcs_lo, *bcs_hi;   // Dirichlet boundary-face states or halo arrays of
+                                     // axis D, or nullptr
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
     int count_cells;       // 1: count the non-physical cells this sweep owns (one
@@ -47,19 +49,24 @@ struct FaceArgs {
 // state defines the (possibly ghost) cell j, and the rule to apply to it:
 // 0 copy, 1 slip-wall mirror (wall-normal momentum negated), 2 no-slip
 // mirror (all momentum negated), 3 / 4 Dirichlet reflection about the low /
-// high boundary-face state.  The final clamp only matters for padding cells
-// beyond the last face of a tile.
-__device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int lo, int hi, int &rule)
+// high boundary-face state; or, for a side whose ghost cells are a
+// neighbouring sub-domain's cells (TENO_BC_HALO), rule 5 / 6 and the plane of
+// the side's halo array (0 .. H-1 in ascending position: cell -H + q below,
+// n + q above).  The final clamps only matter for padding cells beyond the
+// last face of a tile.
+__device__ __forceinline__ int64_t map_index(int64_t j, int64_t n, int H, int lo, int hi, int &rule)
 {
     rule = 0;
     int64_t r = j;
     if (j < 0) {
         if (lo == 0) r = ((j % n) + n) % n;
         else if (lo == 1) r = 0;
+        else if (lo == 5) { rule = 5; r = j + H; return r < 0 ? 0 : r; }
         else { rule = lo == 2 ? 1 : (lo == 3 ? 2 : 3); r = -j - 1; }
     } else if (j >= n) {
         if (hi == 0) r = j % n;
         else if (hi == 1) r = n - 1;
+        else if (hi == 5) { rule = 6; r = j - n; return r >= H ? H - 1 : r; }
         else { rule = hi == 2 ? 1 : (hi == 3 ? 2 : 4); r = 2 * n - 1 - j; }
     }
     return r < 0 ? 0 : (r >= n ? n - 1 : r);
@@ -186,25 +193,36 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         const int64_t pg = pstart + p;
         if (pg >= npen) continue;
         int rule;
-        const int64_t gi = map_index(f0 - H + j, nD, a.bc_lo, a.bc_hi, rule);
-        int64_t id;
-        if (D == 0) id = gi + n0 * (pg + n1 * z);
-        else if (D == 1) id = pg + n0 * (gi + n1 * z);
-        else id = pg + n0 * (y + n1 * gi);
+        const int64_t gi = map_index(f0 - H + j, nD, H, a.bc_lo, a.bc_hi, rule);
         double Uc[nc];
-#pragma unroll
-        for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
         CellQ<ND> q;
-        if (!rule && a.P) {
-            cell_from_prims<ND, D>(Uc, a.P, a.ncell, id, q);      // stored for this input
-        } else {
-            if (rule) {
-                // boundary-face index among the faces of this side (other axes, x fastest)
-                const int64_t m = a.ncell / nD;
-                const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
-                apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
-            }
+        if (rule >= 5) {
+            // a neighbouring sub-domain's cell from the side's halo array,
+            // [nc][H planes][cells of a plane, the other axes x fastest]
+            const int64_t m = a.ncell / nD;
+            const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
+            const double *hb = rule == 5 ? a.bcs_lo : a.bcs_hi;
+#pragma unroll
+            for (int c = 0; c < nc; c++) Uc[c] = hb[((int64_t)c * H + gi) * m + sf];
             cell_quantities<ND, D>(Uc, a.K, q);
+        } else {
+            int64_t id;
+            if (D == 0) id = gi + n0 * (pg + n1 * z);
+            else if (D == 1) id = pg + n0 * (gi + n1 * z);
+            else id = pg + n0 * (y + n1 * gi);
+#pragma unroll
+            for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
+            if (!rule && a.P) {
+                cell_from_prims<ND, D>(Uc, a.P, a.ncell, id, q);      // stored for this input
+            } else {
+                if (rule) {
+                    // boundary-face index among the faces of this side (other axes, x fastest)
+                    const int64_t m = a.ncell / nD;
+                    const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
+                    apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
+                }
+                cell_quantities<ND, D>(Uc, a.K, q);
+            }
         }
         if (a.count_cells) {
             // interior cells of this tile's own face range: each cell once
@@ -488,6 +506,9 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #pragma unroll
             for (int c = 0; c < nc; c++) Fo[c] = FL[c] + thp * dF[c];
         }
+        if (a.limrec) a.limrec[flin] = thp < 1.0 ? 1 : 0;
+    } else if (a.limrec) {
+        a.limrec[flin] = 0;
     }
 
 #pragma unroll

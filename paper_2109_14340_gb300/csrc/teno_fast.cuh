@@ -260,21 +260,22 @@ __device__ __forceinline__ float pow7_sum2(float a, float b0, float b1, bool up)
 // bound of the sum is at most thr, reject when its lower bound exceeds
 // thr_rej; x_L = beta_L + eps with the upper bound raised to tiny2 and the
 // lower bound required to reach it.  x0..x2 / X0..X2: lower / upper bounds of
-// the small stencils' x_k.  Returns L - 2 of the accepted stencil, 0 when
-// all are rejected, -1 when uncertain.
+// the small stencils' x_k; lo, hi: the bounds of beta_L.  Returns L - 2 of
+// the accepted stencil, 0 when all are rejected, -1 when uncertain.
 template <int H, int L>
-__device__ __forceinline__ int select_large(const float (&f)[2 * H], float tiny2, float x0, float x1,
-                                            float x2, float X0, float X1, float X2, float thr,
-                                            float thr_rej)
+__device__ __forceinline__ int select_large(const float (&f)[2 * H], float lo, float hi, float tiny2,
+                                            float x0, float x1, float x2, float X0, float X1,
+                                            float X2, float thr, float thr_rej)
 {
-    float lo, hi;
-    beta_large_bounds<H, L>(f, lo, hi);
     if (pow7_sum(fmaxf(hi, tiny2), x0, x1, x2, true) <= thr) return L - 2;
     if (!(lo >= tiny2) || !(pow7_sum(lo, X0, X1, X2, false) > thr_rej)) return -1;
-    if constexpr (L > 3)
-        return select_large<H, L - 1>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
-    else
+    if constexpr (L > 3) {
+        float lo1, hi1;
+        beta_large_bounds<H, L - 1>(f, lo1, hi1);
+        return select_large<H, L - 1>(f, lo1, hi1, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+    } else {
         return 0;
+    }
 }
 
 // The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
@@ -361,13 +362,11 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     // C_T the parameters allow (the exponent's lower bound, at g = 0), which
     // leaves the eta measure out for most reconstructions.  The C_T bits of
     // the byte are then zero (the byte is not stored).
-    if (!need_ct) {
-        float lo, hi;
-        beta_large_bounds<H, H>(f, lo, hi);
-        if (pow7_sum(fmaxf(hi, tiny2), x0, x1, x2, true) <= F.thr[F.nexp_min]) {
-            flag = (uint8_t)large_code(H);
-            return true;
-        }
+    float blo, bhi;                           // bounds of beta_p, for both tests
+    beta_large_bounds<H, H>(f, blo, bhi);
+    if (!need_ct && pow7_sum(fmaxf(bhi, tiny2), x0, x1, x2, true) <= F.thr[F.nexp_min]) {
+        flag = (uint8_t)large_code(H);
+        return true;
     }
 
     // eta measure over cells -1..2 from the differences Delta_{m+1/2}, m=-2..2.
@@ -410,7 +409,7 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const float thr = F.thr[nexp], thr_rej = F.thr_rej[nexp];
 
     // Targeted selection, largest group first (Sec. 3.3).
-    const int sel = select_large<H, H>(f, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+    const int sel = select_large<H, H>(f, blo, bhi, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
     if (sel < 0) return false;
     if (sel > 0) {
         if constexpr (H == 6)

@@ -54,7 +54,7 @@ def test_workspace_sizing(lib):
     nc, cells = 5, 16 * 12 * 10
     faces = 17 * 12 * 10 + 16 * 13 * 10 + 16 * 12 * 11
     assert nb >= 8 * nc * (cells + faces) + 256
-    assert lib.teno_flags_bytes(p) == faces * (nc * 2 + 2)
+    assert lib.teno_flags_bytes(p) == faces * (nc * 2 + 2 + 1)
 
 
 @pytest.mark.parametrize("bad", [

@@ -105,6 +105,9 @@ def test_flop_accounting_reads_the_s6_code():
     # S6: the common part, one indicator of 11 non-zero shifted values
     # (11 + 121 + 21 flops), its test (8) and its 12-point scheme (23)
     assert bench.recon_flops(6, 4) == 101 + 153 + 8 + 23
-    assert bench.value_flops(6, 4) == 23
+    # the executed count: a decided S6 value is one multiply and 11 fmas
+    t0, _ = bench.face_fp64_instructions(3, 6, [0, 0, 0, 0, 0], 0.0)
+    t1, _ = bench.face_fp64_instructions(3, 6, [0, 0, 0, 0, 1.0], 0.0)
+    assert (t1["dmul"] - t0["dmul"], t1["dfma"] - t0["dfma"]) == (10, 110)
     # the S5 path of TENO12 first tests S6, then S5
     assert bench.recon_flops(6, 3) == 101 + 153 + 8 + (9 + 81 + 17) + 8 + 19

@@ -139,11 +139,37 @@ def test_rhs_parity_limiter(which):
     pg, po = both_params(c, limiter=1)
     dt, _, _ = oracle.cfl_dt(po, c["U"], 0.4)
     r_g, f_g, nb_g = gpu_rhs(pg, c["U"], dt)
-    r_o, f_o, _, nb_o = oracle.rhs(po, c["U"], dt, want_flags=True)
+    r_o, f_o, lf_o, nb_o = oracle.rhs(po, c["U"], dt, want_flags=True)
+    _, _, lim0, tot = T.record_layout(pg)
+    assert f_g.size == tot
+    lf_g = f_g[lim0:]                     # part 3: where the limiter bound
     f_g = f_g[:f_o.size]
     assert nb_g == nb_o
     assert np.count_nonzero(f_g != f_o) == 0
+    assert np.array_equal(lf_g, lf_o)
     assert rel_err(r_g, r_o) <= 1e-12
+    assert np.array_equal(r_g, r_o)
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+def test_limiter_record_parity(scheme):
+    """The double rarefaction (near vacuum at the centre, Sec. 5.3) after four
+    oracle steps, where the limiter binds on some faces: the limiter part of
+    the decision record names the same faces as the oracle's, and the RHS
+    and decision bytes are bitwise the oracle's."""
+    c = workloads.double_rarefaction_1d(200, scheme=scheme)
+    pg, po = both_params(c, limiter=1)
+    U = c["U"].copy()
+    for _ in range(4):
+        dt, _, _ = oracle.cfl_dt(po, U, 0.4)
+        U, _ = oracle.rk3_step(po, U, dt)
+    dt, _, _ = oracle.cfl_dt(po, U, 0.4)
+    r_g, f_g, nb_g = gpu_rhs(pg, U, dt)
+    r_o, f_o, lf_o, nb_o = oracle.rhs(po, U, dt, want_flags=True)
+    assert lf_o.sum() > 0
+    assert np.array_equal(f_g[T.record_layout(pg)[2]:], lf_o)
+    assert np.array_equal(f_g[:f_o.size], f_o)
+    assert nb_g == nb_o
     assert np.array_equal(r_g, r_o)
 
 
@@ -151,8 +177,10 @@ def test_rhs_parity_limiter_2d():
     c = workloads.quadrants_2d(24, 20, scheme=8)
     pg, po = both_params(c, limiter=1)
     dt, _, _ = oracle.cfl_dt(po, c["U"], 0.4)
-    r_g, _, _ = gpu_rhs(pg, c["U"], dt)
-    r_o, _, _, _ = oracle.rhs(po, c["U"], dt)
+    r_g, f_g, _ = gpu_rhs(pg, c["U"], dt)
+    r_o, f_o, lf_o, _ = oracle.rhs(po, c["U"], dt, want_flags=True)
+    assert np.array_equal(f_g[:f_o.size], f_o)
+    assert np.array_equal(f_g[T.record_layout(pg)[2]:], lf_o)
     assert rel_err(r_g, r_o) <= 1e-12
     assert np.array_equal(r_g, r_o)
 

@@ -48,6 +48,8 @@ extern "C" {
                                   this library waits on a flag, a peer or a
                                   barrier outside its own block (the batched
                                   work list is an atomic counter)             */
+#define TENO_EBOUNDS 5         /* teno_debug_bounds: the bounds-checked build
+                                  found an index outside its array           */
 
 /* Boundary conditions per axis side (App. A). */
 #define TENO_BC_PERIODIC 0     /* App. A.4: ghost -r = cell n-r (both sides)  */
@@ -399,6 +401,23 @@ int teno_set_decision_filter(int on);
  * support. */
 int teno_profile_enable(int on);
 int teno_profile_read(double *ms, int64_t *launches, int64_t *faces, int64_t *exact_recons);
+
+/* Bounds-checked build (libteno_gb300_debug.so, compiled with
+ * -DTENO_DEBUG_BOUNDS; the same entry points): every global-memory index of
+ * the face sweeps, the combine and the primitives kernel, and the sweeps'
+ * shared-memory queue indices, are range-checked on the device; an index
+ * outside its array is counted in the workspace's status block and the
+ * access is skipped or redirected to an element inside the array (a load
+ * gives 0), never faulting.  teno_debug_bounds synchronises the stream,
+ * reads and clears that record: the number of such accesses, and the first
+ * one's source line, index and array extent (any pointer may be NULL).
+ * Returns TENO_EBOUNDS if there were any, else TENO_OK (always TENO_OK in the
+ * release build, which has no checks).  teno_build_flags: bit 0 set in the
+ * bounds-checked build.  The paper has no counterpart: these are test
+ * support. */
+int teno_debug_bounds(void *ws, void *stream, int64_t *count, int64_t *line, int64_t *index,
+                      int64_t *extent);
+int teno_build_flags(void);
 
 /* Human-readable text of a return code (static storage). */
 const char *teno_strerror(int code);

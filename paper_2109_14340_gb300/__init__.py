@@ -17,7 +17,7 @@ import threading
 
 from . import _build
 
-TENO_OK, TENO_EINVAL, TENO_ECUDA, TENO_ENONPHYSICAL, TENO_ETIMEOUT = 0, 1, 2, 3, 4
+TENO_OK, TENO_EINVAL, TENO_ECUDA, TENO_ENONPHYSICAL, TENO_ETIMEOUT, TENO_EBOUNDS = 0, 1, 2, 3, 4, 5
 TENO_BC_PERIODIC, TENO_BC_TRANSMISSIVE, TENO_BC_SLIPWALL = 0, 1, 2
 TENO_BC_NOSLIP, TENO_BC_DIRICHLET, TENO_BC_HALO = 3, 4, 5
 TENO_SPLIT_LLF, TENO_SPLIT_RUSANOV = 0, 1
@@ -59,7 +59,10 @@ class teno_params(ctypes.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library load() opens: the bounds-checked build when the
+    environment sets TENO_GB300_DEBUG=1 (built by _build.build(debug=True)),
+    else the release build."""
+    return _build.DEBUG_LIB if os.environ.get("TENO_GB300_DEBUG") == "1" else _build.LIB
 
 
 def load():
@@ -68,10 +71,12 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError("libteno_gb300.so is not built (run __graft_entry__.build() or "
-                               "paper_2109_14340_gb300._build.build()); there is no fallback")
-        lib = ctypes.CDLL(_build.LIB)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built (run __graft_entry__.build() or "
+                               "paper_2109_14340_gb300._build.build()); there is no fallback"
+                               % os.path.basename(path))
+        lib = ctypes.CDLL(path)
         P = ctypes.POINTER(teno_params)
         vp, sz = ctypes.c_void_p, ctypes.c_size_t
         lib.teno_params_init.argtypes = [P]
@@ -112,6 +117,9 @@ def load():
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.teno_debug_bounds.argtypes = [vp, vp, i64p, i64p, i64p, i64p]
+        lib.teno_build_flags.argtypes = []
         lib.teno_strerror.argtypes = [ctypes.c_int]
         lib.teno_strerror.restype = ctypes.c_char_p
         for name in ("teno_workspace_bytes", "teno_flags_bytes", "teno_rhs", "teno_rk3_step",
@@ -121,7 +129,7 @@ def load():
                      "teno_batch_times", "teno_adjoint_workspace_bytes", "teno_rhs_vjp",
                      "teno_rk3_step_record", "teno_rk3_step_vjp", "teno_rhs_frozen",
                      "teno_rk3_step_frozen", "teno_rk3_stage", "teno_wave_speeds",
-                     "teno_dt_from_speeds"):
+                     "teno_dt_from_speeds", "teno_debug_bounds", "teno_build_flags"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -135,7 +143,8 @@ EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno
            "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy",
            "teno_adjoint_workspace_bytes", "teno_rhs_vjp", "teno_rk3_step_record",
            "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen",
-           "teno_rk3_stage", "teno_wave_speeds", "teno_dt_from_speeds")
+           "teno_rk3_stage", "teno_wave_speeds", "teno_dt_from_speeds", "teno_debug_bounds",
+           "teno_build_flags")
 
 TENO_RHS_STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -272,6 +281,21 @@ def teno_dt_from_speeds(p, amax_device, ncopies, cfl, dt_device, stream=None):
 def teno_cfl_dt(p, U, cfl, dt_device, ws=None, stream=None):
     _check(load().teno_cfl_dt(ctypes.byref(p), _ptr(U), float(cfl), _ptr(dt_device), _ptr(ws),
                               ws.numel() * ws.element_size(), _stream(stream)), "teno_cfl_dt")
+
+
+def teno_debug_bounds(ws, stream=None):
+    """(count, source line, index, extent) of the out-of-range accesses the
+    bounds-checked build recorded in this workspace (cleared by the call)."""
+    c, l, i, e = (ctypes.c_int64() for _ in range(4))
+    code = load().teno_debug_bounds(_ptr(ws), _stream(stream), ctypes.byref(c), ctypes.byref(l),
+                                    ctypes.byref(i), ctypes.byref(e))
+    if code not in (TENO_OK, TENO_EBOUNDS):
+        raise TenoError(code, "teno_debug_bounds")
+    return c.value, l.value, i.value, e.value
+
+
+def teno_build_flags() -> int:
+    return int(load().teno_build_flags())
 
 
 def teno_status(ws, stream=None):

@@ -16,6 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libteno_gb300.so")
+DEBUG_LIB = os.path.join(BUILD, "libteno_gb300_debug.so")   # -DTENO_DEBUG_BOUNDS
 PROBE_LIB = os.path.join(BUILD, "libteno_probe.so")
 PROBE_SRC = os.path.join(PKG, "probe", "fp64_probe.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -57,16 +58,21 @@ def build_probe(force: bool = False) -> str:
     return PROBE_LIB
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build libteno_gb300.so, or with debug=True the bounds-checked
+    libteno_gb300_debug.so (the same sources with -DTENO_DEBUG_BOUNDS)."""
+    lib = DEBUG_LIB if debug else LIB
+    odir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(odir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
     nv = _nvcc()
     objs = []
+    extra = ["-DTENO_DEBUG_BOUNDS"] if debug else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nv] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(odir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nv] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))
@@ -76,13 +82,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

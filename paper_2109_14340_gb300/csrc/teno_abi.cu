@@ -3,6 +3,7 @@
 //   [wave maxima] -> prepare -> face sweep x [-> y [-> z]] -> combine.
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t y = blockIdx.y, z = blockIdx.z;
     bool bad = false;
-    if (x < a.n[0]) {
+    if (x < a.n[0] && TENO_IN(a.st, x + a.n[0] * (y + a.n[1] * z), a.ncell)) {
         const int64_t id = x + a.n[0] * (y + a.n[1] * z);
         int64_t flo[3];
 #pragma unroll
@@ -85,7 +86,8 @@ __global__ void __launch_bounds__(256) combine_kernel(CombineArgs a)
                 const int64_t xd = (d == 0) ? x : (d == 1 ? y : z);
                 const int64_t fr = (a.wrap[d] && xd == a.n[d] - 1) ? flo[d] - xd * a.fstride[d]
                                                                     : flo[d] + a.fstride[d];
-                const double t = (Fd[fr] - Fd[flo[d]]) * a.inv_dx[d];
+                const double t = (TENO_LOAD(a.st, Fd, fr, a.nfaces[d]) -
+                                  TENO_LOAD(a.st, Fd, flo[d], a.nfaces[d])) * a.inv_dx[d];
                 acc = acc - t;
             }
             double o;
@@ -851,6 +853,35 @@ int teno_profile_read(double *ms, int64_t *launches, int64_t *faces, int64_t *ex
     return TENO_OK;
 }
 
+int teno_debug_bounds(void *ws, void *stream, int64_t *count, int64_t *line, int64_t *index,
+                      int64_t *extent)
+{
+    if (check_ptr(ws)) return TENO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Status *st = (Status *)ws;
+    long long rec[4] = {0, 0, 0, 0};   // count, line, index, extent (contiguous in Status)
+    static_assert(offsetof(Status, oob_line) == offsetof(Status, oob_count) + 8 &&
+                      offsetof(Status, oob_extent) == offsetof(Status, oob_count) + 24,
+                  "bounds record layout");
+    CUDA_TRY(cudaMemcpyAsync(rec, &st->oob_count, sizeof(rec), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemsetAsync(&st->oob_count, 0, sizeof(rec), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (count) *count = rec[0];
+    if (line) *line = rec[1];
+    if (index) *index = rec[2];
+    if (extent) *extent = rec[3];
+    return rec[0] ? TENO_EBOUNDS : TENO_OK;
+}
+
+int teno_build_flags(void)
+{
+#ifdef TENO_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char *teno_strerror(int code)
 {
     switch (code) {
@@ -860,6 +891,7 @@ const char *teno_strerror(int code)
     case TENO_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0, non-finite value or "
                                    "non-positive Roe sound speed squared)";
     case TENO_ETIMEOUT: return "bounded device wait timed out";
+    case TENO_EBOUNDS: return "out-of-range index found by the bounds-checked build";
     default: return "unknown error code";
     }
 }

@@ -19,9 +19,40 @@ struct Status {
     double dt;                     // time step of the current call
     double lam[3];                 // limiter: effective dt/dx of each direction
     double t_accum;                // summed dt of teno_advance_host
-    double pad[23];
+    unsigned long long oob_count;  // debug build: out-of-range accesses skipped
+    long long oob_line, oob_index, oob_extent;   // the first one's source line, index, extent
+    double pad[19];
 };
 static_assert(sizeof(Status) == 256, "status block is 256 bytes");
+
+// Debug build (-DTENO_DEBUG_BOUNDS): every global-memory index of the face
+// sweeps, the combine and the primitives kernel, and the face sweeps'
+// shared-memory queue indices, are range-checked.  An index outside its
+// array is counted in the status block (with the first offender's source
+// line, index and extent), and the access is skipped -- a load gives 0 --
+// instead of faulting (teno_debug_bounds reads the record).  In the
+// release build the checks compile away.
+#ifdef TENO_DEBUG_BOUNDS
+static __device__ __noinline__ void bounds_fault(Status *st, int line, long long idx, long long n)
+{
+    if (atomicAdd(&st->oob_count, 1ull) == 0ull) {
+        st->oob_line = line;
+        st->oob_index = idx;
+        st->oob_extent = n;
+    }
+}
+#define TENO_IN(st, i, n)                                                                  \
+    (((long long)(i) >= 0 && (long long)(i) < (long long)(n))                              \
+         ? true                                                                            \
+         : (::teno::bounds_fault((st), __LINE__, (long long)(i), (long long)(n)), false))
+#else
+#define TENO_IN(st, i, n) true
+#endif
+#define TENO_LOAD(st, a, i, n) (TENO_IN(st, i, n) ? (a)[i] : 0)
+#define TENO_STORE(st, a, i, n, v)                                                         \
+    do {                                                                                   \
+        if (TENO_IN(st, i, n)) (a)[i] = (v);                                               \
+    } while (0)
 
 // Optimal linear schemes on the large stencils (Sec. 4.1, Eqs. 6-, 8-,
 // 10-point), ascending offsets -2..3, -3..4, -4..5.  The twelve-point S6

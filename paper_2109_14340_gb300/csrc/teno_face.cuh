@@ -202,24 +202,28 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             const int64_t m = a.ncell / nD;
             const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
             const double *hb = rule == 5 ? a.bcs_lo : a.bcs_hi;
+            const int64_t ih = gi * m + sf;
+            const bool ok = TENO_IN(a.st, ih, H * m);
 #pragma unroll
-            for (int c = 0; c < nc; c++) Uc[c] = hb[((int64_t)c * H + gi) * m + sf];
+            for (int c = 0; c < nc; c++) Uc[c] = ok ? hb[(int64_t)c * H * m + ih] : 0.0;
             cell_quantities<ND, D>(Uc, a.K, q);
         } else {
             int64_t id;
             if (D == 0) id = gi + n0 * (pg + n1 * z);
             else if (D == 1) id = pg + n0 * (gi + n1 * z);
             else id = pg + n0 * (y + n1 * gi);
+            const bool ok = TENO_IN(a.st, id, a.ncell);
 #pragma unroll
-            for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
-            if (!rule && a.P) {
+            for (int c = 0; c < nc; c++) Uc[c] = ok ? a.U[c * a.ncell + id] : 0.0;
+            if (!rule && a.P && ok) {
                 cell_from_prims<ND, D>(Uc, a.P, a.ncell, id, q);      // stored for this input
             } else {
                 if (rule) {
                     // boundary-face index among the faces of this side (other axes, x fastest)
                     const int64_t m = a.ncell / nD;
                     const int64_t sf = (D == 0) ? pg + n1 * z : (D == 1 ? pg + n0 * z : pg + n0 * y);
-                    apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
+                    if (rule < 3 || TENO_IN(a.st, sf, m))
+                        apply_ghost_rule<ND, D>(Uc, rule, a.bcs_lo, a.bcs_hi, m, sf, a.K.gm1);
                 }
                 cell_quantities<ND, D>(Uc, a.K, q);
             }
@@ -278,9 +282,13 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         if (D == 0) flin = f + (n0 + 1) * (pstart + p + n1 * z);
         else if (D == 1) flin = pstart + p + n0 * (f + (n1 + 1) * z);
         else flin = pstart + p + n0 * (y + n1 * f);
+        if (!TENO_IN(a.st, flin, a.nfaces)) flin = 0;        // debug build: counted, redirected
         // Splitting speeds over the stencil (first maximum), or at recorded cells.
         if (a.frozen_argmax) {
-            const unsigned w = a.frozen_argmax[flin];
+            unsigned w = a.frozen_argmax[flin];
+            if (!TENO_IN(a.st, (int)(w & 15), W) || !TENO_IN(a.st, (int)((w >> 4) & 15), W) ||
+                !TENO_IN(a.st, (int)((w >> 8) & 15), W) || !TENO_IN(a.st, (int)(w >> 12), W))
+                w = 0;
             am = SQ(SL::QLM, fo + (int)(w & 15), p);
             a0 = SQ(SL::QL0, fo + (int)((w >> 4) & 15), p);
             ap = SQ(SL::QLP, fo + (int)((w >> 8) & 15), p);
@@ -368,7 +376,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                     val = flux_large<H, H>(v);
                 } else {
                     int q = atomicAdd(&qcount[dec ? 1 : 0], 1);
-                    const bool room = dec ? (q < CAP - QE) : (q < QE);
+                    const bool room = (dec ? (q < CAP - QE) : (q < QE)) &&
+                                      TENO_IN(a.st, q + (dec ? QE : 0), CAP);
                     if (room) {
                         if (dec) {
                             q += QE;
@@ -402,8 +411,11 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             uint8_t fl;
             const double r = teno_recon<H>(v, a.K, fl);
             const int meta = Qmeta[q];
-            Qres[(meta >> 4) * (2 * nc) + (meta & 15)] = r;
-            Qfl[(meta >> 4) * (2 * nc) + (meta & 15)] = fl;
+            const int slot = (meta >> 4) * (2 * nc) + (meta & 15);
+            if (TENO_IN(a.st, slot, TP * TF * 2 * nc)) {
+                Qres[slot] = r;
+                Qfl[slot] = fl;
+            }
         }
         for (int q = QE + threadIdx.x; q < QE + nd; q += TP * TF) {
             double v[W];
@@ -411,7 +423,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             for (int kk = 0; kk < W; kk++) v[kk] = Qv[(size_t)q * W + kk];
             const int meta = Qmeta[q];
             const int slot = (meta >> 4) * (2 * nc) + (meta & 15);
-            Qres[slot] = decided_value<H>(v, Qfl[slot]);
+            if (TENO_IN(a.st, slot, TP * TF * 2 * nc)) Qres[slot] = decided_value<H>(v, Qfl[slot]);
         }
         __syncthreads();
         if (active && pending) {

@@ -82,12 +82,15 @@ def test_noh_analytic_solution(scheme):
     cc = (np.arange(n) + 0.5) * dx
     Z, Y, X = np.meshgrid(cc, cc, cc, indexing="ij")
     r = np.sqrt(X * X + Y * Y + Z * Z).ravel()
-    rho = U[0].cpu().numpy()
+    Uh = U.cpu().numpy()
+    rho = Uh[0]
+    pres = (c["gamma"] - 1.0) * (Uh[4] - 0.5 * (Uh[1:4] ** 2).sum(axis=0) / rho)
     R = t / 3.0
     # shell averages, one cell wide, inside the inscribed sphere r < L
     shell = np.floor(r / dx).astype(int)
     k = np.arange(int(L / dx))
     prof = np.array([rho[shell == i].mean() for i in k])
+    pprof = np.array([pres[shell == i].mean() for i in k])
     rc = np.array([r[shell == i].mean() for i in k])
     ex = workloads.noh_density(rc, t)
     # the shock: the shell profile crosses 40 (between 16 ahead, 64 behind) at t/3
@@ -97,13 +100,18 @@ def test_noh_analytic_solution(scheme):
     post = (rc > 0.4 * R) & (rc < R - 4 * dx)
     pre_err = np.abs(prof[pre] - ex[pre]) / ex[pre]
     post_mean = prof[post].mean()
+    post_p = pprof[post].mean()                  # exact: 64/3 behind the shock
     cell_pre = r > R + 6 * dx
     scatter = np.percentile(np.abs(rho[cell_pre] - workloads.noh_density(r[cell_pre], t))
                             / workloads.noh_density(r[cell_pre], t), 99)
     print("noh scheme %d: r40 %.4f (t/3 %.4f), pre-shock shell error max %.4f mean %.4f, "
-          "post-shock mean %.2f, cell scatter p99 %.3f" % (scheme, r40, R, pre_err.max(),
-                                                           pre_err.mean(), post_mean, scatter))
+          "post-shock density %.2f pressure %.3f, cell scatter p99 %.3f"
+          % (scheme, r40, R, pre_err.max(), pre_err.mean(), post_mean, post_p, scatter))
     assert abs(r40 - R) <= 2.5 * dx
     assert pre_err.max() <= 0.05
-    assert abs(post_mean - 64.0) <= 0.1 * 64.0
-    assert scatter <= 0.35
+    # the plateau and the pressure converge slowly with the cell size (the
+    # start-up error of the singular initial state moves the shock ahead);
+    # at 64^3 both sit 4-6 % low
+    assert abs(post_mean - 64.0) <= 0.07 * 64.0
+    assert abs(post_p - 64.0 / 3.0) <= 0.07 * 64.0 / 3.0
+    assert scatter <= 0.30

@@ -571,6 +571,9 @@ def run_adjoint(args, dev, stream):
             "fd_frozen_decisions_max_rel_err": max(errs),
             "fd_frozen_decisions_median_rel_err": float(sorted(errs)[len(errs) // 2]),
             "fd_directions": len(errs),
+            "vjp_face_kernel_fp64_pipe_busy": read_adjoint_fp64_busy(),
+            "vjp_face_kernel_fp64_pipe_busy_source": "ncu, profiles/adjoint_2d.md (512^2, the "
+                                                     "two reverse face sweeps averaged)",
             "loss": float(loss.detach())}
 
 
@@ -727,6 +730,16 @@ def measured_hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def read_adjoint_fp64_busy():
+    """The reverse face kernel's FP64-pipe busy fraction from the committed
+    ncu summary (a line 'fp64_pipe_busy[adj_face_kernel]: <value>')."""
+    path = os.path.join(ROOT, "profiles", "adjoint_2d.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"fp64_pipe_busy\[adj_face_kernel\]:\s*([0-9.eE+-]+)", open(path).read())
+    return float(m.group(1)) if m else None
+
+
 def read_traffic_per_face(scheme):
     """Measured DRAM bytes per face of the face sweep, from the committed ncu
     summary (a line 'traffic_bytes_per_face[TENO<s>]: <value>')."""
@@ -764,7 +777,6 @@ def run_ours(args, rank, world, local_rank):
                            bc_lo=[0, 0, 0], bc_hi=[0, 0, 0])
     solver = T.Solver(p, dev)
     U = torch.from_numpy(case["U"]).to(dev)
-    U0 = U.clone()
     cells = n ** 3
     stream = torch.cuda.current_stream(dev)
 
@@ -775,6 +787,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize(dev)
+    U_w = U.clone()          # the state the timed steps start from (also the e2e's)
 
     # decision histogram of the current state (untimed) -> algorithmic flops
     _, flags = solver.rhs(U, flags=True)
@@ -805,9 +818,11 @@ def run_ours(args, rank, world, local_rank):
     value = whole_job_rate(world, cells, args.steps, t_max * 1e-3)
 
     # e2e: host buffers through teno_advance_host, one step per call
-    # (H2D of the state, CFL + RK3 step, D2H of the state, every step)
-    Uh = U0.cpu().pin_memory()
-    Ud2 = torch.empty_like(U0)
+    # (H2D of the state, CFL + RK3 step, D2H of the state, every step), from
+    # the state the timed steps started from (the first steps of the field
+    # cost more: its initial small scales take more fallbacks)
+    Uh = U_w.cpu().pin_memory()
+    Ud2 = torch.empty_like(U_w)
     ws2 = torch.zeros_like(solver.ws)
     T.teno_advance_host(p, Uh, Ud2, 1, 0.4, ws2)         # warm
     k_e2e = max(1, min(args.steps, 3))

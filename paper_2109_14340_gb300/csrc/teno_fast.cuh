@@ -101,25 +101,16 @@ inline FastK fastk_make(double cr, double alpha1, double alpha2)
 }
 
 // FP64 -> FP32 with the exponent lowered by `shift` (exact power-of-two
-// scaling), truncating the mantissa.  Scaled magnitudes below 2^-100 become
-// zero (absolute error < 2^-100, which callers add to their bounds); ok =
-// false above 2^100 or for subnormal inputs.
-__device__ __forceinline__ float d2f_scaled(double x, int shift, bool &ok)
+// scaling), truncating the mantissa, for x whose exponent is at most shift
+// (the caller's common scale).  Scaled magnitudes below 2^-100 become zero
+// (absolute error < 2^-100, which callers add to their bounds); so do zero
+// and subnormal x, which the caller's scale (shift >= -100) puts below that.
+__device__ __forceinline__ float d2f_scaled(double x, int shift)
 {
     const int hi = __double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
-    const int e = (hi >> 20) & 0x7FF;
-    if (e == 0) {
-        if ((hi & 0xFFFFF) == 0 && lo == 0) return 0.0f;   // +-0
-        ok = false;
-        return 0.0f;
-    }
-    const int ef = e - 1023 - shift;                         // unbiased scaled exponent
+    const int ef = ((hi >> 20) & 0x7FF) - 1023 - shift;     // unbiased scaled exponent, <= 0
     if (ef < -100) return 0.0f;
-    if (ef > 100) {
-        ok = false;
-        return 0.0f;
-    }
     const unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(ef + 127) << 23) |
                           (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
     return __uint_as_float(bits);
@@ -289,26 +280,26 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     constexpr int W = 2 * H;
 #define SV(m) s[(m) + H - 1]
 #define VV(m) v[(m) + H - 1]
-    // All values bit-identical: every indicator is exactly 0, chi = 1/4,
-    // eta = 1, hence S_p with the smooth exponent.
-    bool all_eq = true;
-#pragma unroll
-    for (int j = 0; j < W; j++) all_eq = all_eq && dbits_equal(v[j], v[H - 1]);
-    if (all_eq) {
-        flag = (uint8_t)(large_code(H) | (((F.nexp_smooth - 7) & 7) << 5));
-        return true;
-    }
     // Common scale: the largest exponent among the shifted values.
     int emax = -1100;
 #pragma unroll
     for (int j = 0; j < W; j++)
         if (j != H - 1 && (__double2hiint(s[j]) & 0x7FF00000) != 0) emax = max(emax, dexp(s[j]));
+    if (emax == -1100) {
+        // No shifted value above the subnormal range.  All values bit-identical:
+        // every indicator is exactly 0, chi = 1/4, eta = 1, hence S_p with the
+        // smooth exponent; anything else goes to the exact path.
+        bool all_eq = true;
+#pragma unroll
+        for (int j = 0; j < W; j++) all_eq = all_eq && dbits_equal(v[j], v[H - 1]);
+        if (!all_eq) return false;
+        flag = (uint8_t)(large_code(H) | (((F.nexp_smooth - 7) & 7) << 5));
+        return true;
+    }
     if (emax < -100 || emax > 50) return false;
-    bool ok = true;
     float f[W];
 #pragma unroll
-    for (int j = 0; j < W; j++) f[j] = (j == H - 1) ? 0.0f : d2f_scaled(s[j], emax, ok);
-    if (!ok) return false;
+    for (int j = 0; j < W; j++) f[j] = (j == H - 1) ? 0.0f : d2f_scaled(s[j], emax);
     // indicator threshold 2^-100 in original units -> scaled units
     const int tb = -100 - 2 * emax;
     const float tiny2 = tb < -126 ? 1.17549435e-38f : __uint_as_float((unsigned)(tb + 127) << 23);
@@ -316,10 +307,11 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const float z100 = 1.6e-30f;             // > 2^-100: flushed-value error
     // The exact path evaluates the small indicators on the unshifted values:
     // its rounding is relative to max |v| (bound 2^(ev - emax - 50) scaled).
-    int ev = -1100;
-#pragma unroll
-    for (int j = 0; j < W; j++)
-        if ((__double2hiint(v[j]) & 0x7FF00000) != 0) ev = max(ev, dexp(v[j]));
+    // |v_m| <= |v_0| + |v_m - v_0| < 2^(e_0 + 1) + 2^(emax + 1) (1 + 2^-52)
+    // with e_0 the exponent of v_0, so ev = max(e_0, emax) + 1 bounds the
+    // exponent of every v_m.
+    const int ecell = (__double2hiint(VV(0)) & 0x7FF00000) != 0 ? dexp(VV(0)) : -1100;
+    const int ev = max(ecell, emax) + 1;
     if (ev - emax > 60) return false;
     const float eo = ev < -900 ? 0.0f : __uint_as_float((unsigned)(max(ev - emax - 50, -126) + 127) << 23);
 #define FF(m) f[(m) + H - 1]

@@ -280,12 +280,15 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     constexpr int W = 2 * H;
 #define SV(m) s[(m) + H - 1]
 #define VV(m) v[(m) + H - 1]
-    // Common scale: the largest exponent among the shifted values.
-    int emax = -1100;
+    // Common scale: the largest exponent among the shifted values (the
+    // largest biased exponent field: zero for zeros and subnormals, 0x7FF for
+    // non-finite values, which the range test below sends on).
+    int efield = 0;
 #pragma unroll
     for (int j = 0; j < W; j++)
-        if (j != H - 1 && (__double2hiint(s[j]) & 0x7FF00000) != 0) emax = max(emax, dexp(s[j]));
-    if (emax == -1100) {
+        if (j != H - 1) efield = max(efield, (__double2hiint(s[j]) >> 20) & 0x7FF);
+    const int emax = efield - 1023;
+    if (efield == 0) {
         // No shifted value above the subnormal range.  All values bit-identical:
         // every indicator is exactly 0, chi = 1/4, eta = 1, hence S_p with the
         // smooth exponent; anything else goes to the exact path.
@@ -356,9 +359,15 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     // the byte are then zero (the byte is not stored).
     float blo, bhi;                           // bounds of beta_p, for both tests
     beta_large_bounds<H, H>(f, blo, bhi);
-    if (!need_ct && pow7_sum(fmaxf(bhi, tiny2), x0, x1, x2, true) <= F.thr[F.nexp_min]) {
-        flag = (uint8_t)large_code(H);
-        return true;
+    if (!need_ct) {
+        // sum_k (x_p / x_k)^7 <= 3 (x_p / min_k x_k)^7: one division for the
+        // common case (a looser bound only sends borderline cases on)
+        const float r = __fdividef(fmaxf(bhi, tiny2), fminf(x0, fminf(x1, x2))) * (1.0f + 5e-7f);
+        const float q = r * r;
+        if (3.0f * (q * q * q * r) * (1.0f + 4e-6f) <= F.thr[F.nexp_min]) {
+            flag = (uint8_t)large_code(H);
+            return true;
+        }
     }
 
     // eta measure over cells -1..2 from the differences Delta_{m+1/2}, m=-2..2.

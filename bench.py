@@ -111,7 +111,7 @@ def _acc(tot, add=0.0, mul=0.0, fma=0.0, div=0.0, sqrt=0.0, w=1.0):
     tot["dfma"] += w * (fma + div * KDIV["dfma"] + sqrt * KSQRT["dfma"])
 
 
-def face_fp64_instructions(nd, H, hist, exact_frac, tf=32, stored_prims=True):
+def face_fp64_instructions(nd, H, hist, exact_frac, tf=32):
     """FP64 instructions the face-sweep kernel executes per face, by kind,
     following its code: staged cells formed from the stored primitives
     (flux, halving, speeds), Roe average and eigenvector rows, projection of
@@ -124,10 +124,7 @@ def face_fp64_instructions(nd, H, hist, exact_frac, tf=32, stored_prims=True):
     nrec = 2 * nc
     t = {"dadd": 0.0, "dmul": 0.0, "dfma": 0.0}
     staged = (tf + W - 1) / tf
-    if stored_prims:
-        _acc(t, add=5, mul=nd + 1 + 2 * nc, w=staged)                   # staged cells
-    else:                                # batched mode: primitives computed while staging
-        _acc(t, add=6, mul=2 * nd + 7 + 2 * nc, fma=nd - 1, div=1, sqrt=2, w=staged)
+    _acc(t, add=5, mul=nd + 1 + 2 * nc, w=staged)                       # staged cells
     _acc(t, add=2, mul=2 * nd + 12, fma=2 * nd, div=2, sqrt=1)         # Roe state
     _acc(t, add=5, mul=5 * nd + 2)                                     # eigenvector rows
     _acc(t, mul=3 * W * 2, fma=3 * W * 2 * (nc - 1))                   # acoustic, entropy
@@ -461,7 +458,7 @@ def run_batched(args, dev, stream):
         H = scheme // 2
         hist = [0.0] * 5
         hist[H - 2] = 1.0
-        ti, _ = face_fp64_instructions(1, H, hist, 0.0, tf=tile, stored_prims=False)
+        ti, _ = face_fp64_instructions(1, H, hist, 0.0, tf=tile)
         nf = 3 * sum(c["n"][0] + 1 for c in cases if c["scheme"] == scheme)
         flops += nf * (ti["dadd"] + ti["dmul"] + 2.0 * ti["dfma"])
         instr += nf * (ti["dadd"] + ti["dmul"] + ti["dfma"])
@@ -487,7 +484,7 @@ def run_batched(args, dev, stream):
                                    "frac": achieved / peak},
                          "counted": "FP64 instructions the three persistent face sweeps of a "
                                     "step execute (largest-stencil value for every "
-                                    "reconstruction, primitives computed while staging), over "
+                                    "reconstruction, primitives read from the stored rows), over "
                                     "the whole step's time: a lower bound"},
             "mode": "persistent (problem, tile) work list, step captured in a CUDA graph"}
 

@@ -18,7 +18,7 @@
 namespace teno {
 
 struct BatchProb {
-    int64_t n, u_off, f_off;
+    int64_t n, u_off, f_off, p_off;   // cells; state, face-flux, primitive-row offsets
     double inv_dx;
     int32_t scheme, limiter, bc_lo, bc_hi;
 };
@@ -44,9 +44,11 @@ __device__ __forceinline__ int find_problem(const int32_t *prefix, int nprob, in
     return lo;
 }
 
+// Per-problem wave-speed maxima of the step's state; the same pass stores its
+// primitives for the first stage's sweep and counts its non-physical cells.
 __global__ void __launch_bounds__(kCellTile) batch_wave_max_kernel(
     const BatchProb *probs, int nprob, const int32_t *cprefix, const double *U, BatchSlot *slots,
-    Consts K)
+    double *P, Status *st, Consts K)
 {
     __shared__ double red[kCellTile / 32];
     const int nitems = cprefix[nprob];
@@ -60,6 +62,8 @@ __global__ void __launch_bounds__(kCellTile) batch_wave_max_kernel(
             double Uc[3] = {Up[i], Up[d.n + i], Up[2 * d.n + i]};
             CellQ<1> q;
             cell_quantities<1, 0>(Uc, K, q);
+            store_prims<1>(q, P + d.p_off, d.n, i);
+            if (nonphysical_cell<1>(Uc[0], q)) atomicAdd(&st->nonphys, 1ull);
             const double e = fabs(q.u[0]) + q.c;
             if (e > m) m = e;
         }
@@ -98,8 +102,8 @@ __global__ void batch_finalize_kernel(const BatchProb *probs, int nprob, BatchSl
 // Registers bounded as for the 2D/3D sweeps: 384 threads' worth of blocks per SM.
 template <int TF>
 __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_kernel(
-    const BatchProb *probs, int nprob, const int32_t *fprefix, const double *U, double *F,
-    BatchSlot *slots, Status *st, Consts K, FastK FK, int fast, int *counter)
+    const BatchProb *probs, int nprob, const int32_t *fprefix, const double *U, const double *P,
+    double *F, BatchSlot *slots, Status *st, Consts K, FastK FK, int fast, int *counter)
 {
     extern __shared__ double sm[];
     __shared__ int s_item;
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         const BatchProb d = probs[p];
         FaceArgs a;
         a.U = U + d.u_off;
-        a.P = nullptr;                      // primitives computed while staging
+        a.P = P + d.p_off;                  // the stage input's stored primitives
         a.F = F + d.f_off;
         a.flags = nullptr;
         a.frozen = nullptr;
@@ -144,10 +148,13 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
 }
 
 // Flux difference and SSP-RK3 stage per cell (the arithmetic of combine_kernel
-// for one 1D problem), with each problem's own dt.
+// for one 1D problem), with each problem's own dt.  Stages 1 and 2 store the
+// new stage state's primitives for the next sweep and count its
+// non-physical cells (the next evaluation's input; the step's own state is
+// counted by the wave-maximum pass).
 __global__ void __launch_bounds__(kCellTile) batch_combine_kernel(
     const BatchProb *probs, int nprob, const int32_t *cprefix, const double *Uk, const double *Un,
-    double *out, const double *F, const BatchSlot *slots, Status *st, Consts K, int mode)
+    double *out, const double *F, const BatchSlot *slots, double *P, Status *st, Consts K, int mode)
 {
     const int nitems = cprefix[nprob];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -158,12 +165,7 @@ __global__ void __launch_bounds__(kCellTile) batch_combine_kernel(
         const double *Ukp = Uk + d.u_off;
         const double *Fp = F + d.f_off;
         double Uc[3] = {Ukp[i], Ukp[d.n + i], Ukp[2 * d.n + i]};
-        {
-            CellQ<1> q;
-            cell_quantities<1, 0>(Uc, K, q);
-            if (!(Uc[0] > 0.0) || !(q.p > 0.0) || !isfinite(q.c) || !isfinite(q.H))
-                atomicAdd(&st->nonphys, 1ull);
-        }
+        double Uo[3];
         const double dt = slots[p].dt;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -177,6 +179,13 @@ __global__ void __launch_bounds__(kCellTile) batch_combine_kernel(
             else if (mode == 2) o = 0.75 * Un[d.u_off + c * d.n + i] + 0.25 * s;
             else o = (1.0 / 3.0) * Un[d.u_off + c * d.n + i] + (2.0 / 3.0) * s;
             out[d.u_off + c * d.n + i] = o;
+            Uo[c] = o;
+        }
+        if (mode < 3) {
+            CellQ<1> q;
+            cell_quantities<1, 0>(Uo, K, q);
+            store_prims<1>(q, P + d.p_off, d.n, i);
+            if (nonphysical_cell<1>(Uo[0], q)) atomicAdd(&st->nonphys, 1ull);
         }
     }
 }
@@ -191,9 +200,9 @@ struct teno_batch {
     std::vector<BatchProb> desc;
     std::vector<int32_t> fprefix[3];
     std::vector<int32_t> cprefix;
-    size_t u_len = 0, f_len = 0;
+    size_t u_len = 0, f_len = 0, p_len = 0;
     size_t off_slots = 0, off_counters = 0, off_desc = 0, off_fprefix[3] = {0, 0, 0},
-           off_cprefix = 0, off_F = 0, off_Us = 0, off_single = 0, total = 0;
+           off_cprefix = 0, off_F = 0, off_Us = 0, off_P = 0, off_single = 0, total = 0;
     size_t single_bytes = 0;
     int tile_idx = 1;           // index into kTiles
     int blocks_per_sm = 2;
@@ -298,10 +307,11 @@ int enqueue_step(teno_batch *b, double *U, double cfl, char *ws, int tile_idx, i
     const int32_t *cpre = (const int32_t *)(ws + b->off_cprefix);
     double *F = (double *)(ws + b->off_F);
     double *Us = (double *)(ws + b->off_Us);
+    double *P = (double *)(ws + b->off_P);
     const int ncitems = b->cprefix[np];
     const int grid_c = std::max(1, std::min(ncitems, b->num_sms * 8));
     CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(int), s));
-    batch_wave_max_kernel<<<grid_c, kCellTile, 0, s>>>(desc, np, cpre, U, slots, K);
+    batch_wave_max_kernel<<<grid_c, kCellTile, 0, s>>>(desc, np, cpre, U, slots, P, st, K);
     CUDA_TRY(cudaGetLastError());
     batch_finalize_kernel<<<(np + 127) / 128, 128, 0, s>>>(desc, np, slots, cfl);
     CUDA_TRY(cudaGetLastError());
@@ -313,17 +323,17 @@ int enqueue_step(teno_batch *b, double *U, double cfl, char *ws, int tile_idx, i
         const double *Uin = stg == 0 ? U : Us;
         if (TF == 64) {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 64>(), face_smem_bytes<1, 4, 1, 64>());
-            batch_face_kernel<64><<<grid_f, 64, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
+            batch_face_kernel<64><<<grid_f, 64, sm, s>>>(desc, np, fpre, Uin, P, F, slots, st, K, FK, fast, counters + stg);
         } else if (TF == 128) {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 128>(), face_smem_bytes<1, 4, 1, 128>());
-            batch_face_kernel<128><<<grid_f, 128, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
+            batch_face_kernel<128><<<grid_f, 128, sm, s>>>(desc, np, fpre, Uin, P, F, slots, st, K, FK, fast, counters + stg);
         } else {
             constexpr size_t sm = std::max(face_smem_bytes<1, 5, 1, 256>(), face_smem_bytes<1, 4, 1, 256>());
-            batch_face_kernel<256><<<grid_f, 256, sm, s>>>(desc, np, fpre, Uin, F, slots, st, K, FK, fast, counters + stg);
+            batch_face_kernel<256><<<grid_f, 256, sm, s>>>(desc, np, fpre, Uin, P, F, slots, st, K, FK, fast, counters + stg);
         }
         CUDA_TRY(cudaGetLastError());
         batch_combine_kernel<<<grid_c, kCellTile, 0, s>>>(desc, np, cpre, Uin, U, stg == 2 ? U : Us, F,
-                                                         slots, st, K, stg + 1);
+                                                         slots, P, st, K, stg + 1);
         CUDA_TRY(cudaGetLastError());
     }
     return TENO_OK;
@@ -360,7 +370,7 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
     b->common = *common;
     b->common.ndim = 1;
     b->probs.assign(probs, probs + nprob);
-    size_t f_off = 0, u_end = 0, single = 0;
+    size_t f_off = 0, p_off = 0, u_end = 0, single = 0;
     int64_t ftiles[3] = {0, 0, 0}, ctiles = 0;
     for (int k = 0; k < 3; k++) b->fprefix[k].push_back(0);
     b->cprefix.push_back(0);
@@ -382,6 +392,7 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
         d.n = q.n;
         d.u_off = q.offset;
         d.f_off = (int64_t)f_off;
+        d.p_off = (int64_t)p_off;
         d.inv_dx = 1.0 / q.dx;
         d.scheme = q.scheme;
         d.limiter = q.limiter;
@@ -390,6 +401,7 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
         b->desc.push_back(d);
         f_off += 3 * (size_t)(q.n + 1);
         f_off = (f_off + 1) & ~(size_t)1;                 // keep 16-byte alignment
+        p_off += (size_t)PrimRows<1>::NP * (size_t)q.n;
         u_end = std::max(u_end, (size_t)(q.offset + 3 * q.n));
         for (int k = 0; k < 3; k++) {
             ftiles[k] += (q.n + 1 + kTiles[k] - 1) / kTiles[k];
@@ -410,6 +422,7 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
         if (iv[i].first < iv[i - 1].second) { delete b; return TENO_EINVAL; }
     b->u_len = u_end;
     b->f_len = f_off;
+    b->p_len = p_off;
     b->single_bytes = single;
     size_t off = a256(sizeof(Status));
     b->off_slots = off;
@@ -428,6 +441,8 @@ int teno_batch_create(const teno_params *common, const teno_batch_problem *probs
     off += a256(sizeof(double) * b->f_len);
     b->off_Us = off;
     off += a256(sizeof(double) * b->u_len);
+    b->off_P = off;
+    off += a256(sizeof(double) * b->p_len);
     b->off_single = off;
     off += a256(single);
     b->total = off;

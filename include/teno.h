@@ -379,9 +379,9 @@ int teno_reconstruct(const teno_params *p, const double *v, int64_t count, doubl
  * evaluation whenever the bounds leave the decision open; 0 always evaluates
  * the decisions in FP64.  Results are identical either way (the filter only
  * answers when its answer equals the FP64 one); the switch exists to test
- * and time that.  The filter's error bounds take the epsilons of Sec. 3.2
- * and Sec. 3.4 as negligible above 2^-100, which holds for eps_beta and
- * eps_eta at most 1e-40 (the paper's value): with a larger epsilon every
+ * and time that.  The filter's error bounds carry the epsilons of Sec. 3.2
+ * and Sec. 3.4 explicitly and are valid for eps_beta and eps_eta in
+ * [0, 1e-40] (the paper's value is 1e-40): with a larger epsilon every
  * decision is evaluated in FP64 whatever the switch says.  Not thread-safe
  * with concurrent launches. */
 int teno_set_decision_filter(int on);

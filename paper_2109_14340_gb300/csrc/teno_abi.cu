@@ -359,7 +359,7 @@ int g_fast_filter = 1;
 
 static FastK fastk_of(const teno_params *p)
 {
-    return fastk_make(p->ct_cr, p->ct_alpha1, p->ct_alpha2);
+    return fastk_make(p->ct_cr, p->ct_alpha1, p->ct_alpha2, p->eps_beta, p->eps_eta);
 }
 
 // The filter runs when it is switched on and its bounds hold for p's epsilons.

@@ -317,7 +317,8 @@ int enqueue_step(teno_batch *b, double *U, double cfl, char *ws, int tile_idx, i
     CUDA_TRY(cudaGetLastError());
     const int TF = kTiles[tile_idx];
     const int grid_f = b->num_sms * bps;
-    const FastK FK = fastk_make(b->common.ct_cr, b->common.ct_alpha1, b->common.ct_alpha2);
+    const FastK FK = fastk_make(b->common.ct_cr, b->common.ct_alpha1, b->common.ct_alpha2,
+                                b->common.eps_beta, b->common.eps_eta);
     const int fast = g_fast_filter && fast_filter_valid(b->common.eps_beta, b->common.eps_eta);
     for (int stg = 0; stg < 3; stg++) {
         const double *Uin = stg == 0 ? U : Us;

@@ -27,11 +27,19 @@
 // 2^-24; conversions from FP64 truncate (relative error < 2^-23); the FP64
 // evaluation of the same formulas differs from the exact value by a few 2^-53,
 // covered by the widening factors.  Operands are scaled by a power of two
-// (exact) so that FP32 never over- or underflows; epsilon = 1e-40 of Eq.
-// scale_separation and of the eta measure is handled by requiring the
-// indicators (in original units) to exceed 2^-100, where it is negligible,
-// and values are kept below 2^51 so that the exact path's 1/(beta+eps)^7
-// neither overflows nor underflows.
+// (exact) so that FP32 never over- or underflows.  The epsilons of Eq.
+// scale_separation and of the eta measure enter the bounds explicitly
+// (x_k = beta_k + eps, eta <= |2ab|/(a^2+b^2) + eps/(a^2+b^2)); every
+// x_k must reach 2^-140 (original units) and values stay below 2^51, so
+// that the exact path's (beta+eps)^7 and its reciprocal are normal numbers.
+//
+// Values that agree to within rounding (a plateau carrying rounding noise,
+// or the LLF split's near-cancelling side there): the exact path evaluates
+// the small indicators on the unshifted values, so its own rounding is as
+// large as the differences.  When the values' exponent exceeds the common
+// scale by 30 or more, the filter takes the small indicators' inputs with
+// the exact path's FP64 operations (bitwise its values) and bounds only
+// their conversion to FP32.
 #pragma once
 
 #include <cmath>
@@ -49,31 +57,41 @@ struct FastK {
                                  // is smaller (g >= 0 and rounding is monotone)
     float thr[23];               // thr[n] <= 1 / (10^-n (1 + 2^-16)) - 1
     float thr_rej[23];           // thr_rej[n] >= 1 / (10^-n (1 - 2^-16)) - 1
+    float eb_lo, eb_hi;          // eps_beta * 2^100 (1 -+ 1e-6) rounded down / up
+    float ee_hi;                 // eps_eta * 2^100 rounded up
 };
 
 // Filter switch (teno_set_decision_filter), process-wide.
 extern int g_fast_filter;
 
-// Whether the filter may decide for these epsilons.  Its bounds treat the
-// epsilon of Eq. scale_separation and that of the eta measure (Sec. 3.4) as
-// negligible next to indicators and squared differences of at least 2^-100
-// (in original units): the upper bounds of x_k = beta_k + eps fold eps in as
-// a relative 1.3e-10, and eta's one-sided bound as 1e-9, both of which need
-// eps <= 1e-40.  The paper's value is 1e-40; larger epsilons (or a NaN) get
-// every decision from the exact FP64 path.  Smaller ones, zero included, are
-// safe: on bit-identical values the exact path's chi is then inf/inf = NaN,
-// which the cut-off test keeps (S_p, as the shortcut answers), and every
-// other certified answer needs the small indicators above 2^-100, where
-// (beta + eps)^7 cannot underflow.
+// Whether the filter may decide for these epsilons.  Its bounds carry the
+// epsilon of Eq. scale_separation and that of the eta measure (Sec. 3.4)
+// explicitly, in units scaled by up to 2^200; eps <= 1e-40 keeps them
+// below 2^67 there, inside the range of FP32 and of its approximate
+// division.  The paper's value is 1e-40; larger epsilons (or a NaN) get
+// every decision from the exact FP64 path.  Smaller ones, zero included,
+// are safe: on bit-identical values the exact path's chi is then inf/inf =
+// NaN, which the cut-off test keeps (S_p, as the shortcut answers), and
+// every other certified answer needs each x_k = beta_k + eps at 2^-140 or
+// above, where (beta + eps)^7 cannot underflow.
 inline bool fast_filter_valid(double eps_beta, double eps_eta)
 {
     return eps_beta >= 0.0 && eps_beta <= 1e-40 && eps_eta >= 0.0 && eps_eta <= 1e-40;
 }
 
-// Host: constants of the filter for given C_T parameters.
-inline FastK fastk_make(double cr, double alpha1, double alpha2)
+// Host: constants of the filter for given C_T parameters and epsilons.
+inline FastK fastk_make(double cr, double alpha1, double alpha2, double eps_beta, double eps_eta)
 {
     FastK F;
+    const double s100 = 1267650600228229401496703205376.0;      // 2^100
+    const double eb = eps_beta * s100, ee = eps_eta * s100;
+    const double ebl = eb * (1.0 - 1.0e-6), ebh = eb * (1.0 + 1.0e-6);   // x_lower / x_upper
+    F.eb_lo = (float)ebl;
+    if ((double)F.eb_lo > ebl) F.eb_lo = nextafterf(F.eb_lo, 0.0f);
+    F.eb_hi = (float)ebh;
+    if ((double)F.eb_hi < ebh) F.eb_hi = nextafterf(F.eb_hi, INFINITY);
+    F.ee_hi = (float)ee;
+    if ((double)F.ee_hi < ee) F.ee_hi = nextafterf(F.ee_hi, INFINITY);
     const double inv = 1.0 / cr;
     F.cr_inv_lo = nextafterf((float)inv, 0.0f);
     F.cr_inv_hi = nextafterf((float)inv, 1e30f);
@@ -128,15 +146,19 @@ __device__ __forceinline__ bool dbits_equal(double a, double b)
 
 // Bounds [lo, hi] of eta = (|2ab| + eps)/(a^2 + b^2 + eps) from FP32 values
 // a, b with absolute error bounds ea, eb (scaled units), and the exact-zero
-// knowledge of the FP64 differences.  tiny: scaled 2^-100 threshold.
+// knowledge of the FP64 differences.  With N = |2ab| <= D = a^2 + b^2,
+// eta - N/D = eps (D - N) / (D (D + eps)) lies in [0, eps/D]; eps_hi: an
+// upper bound of the scaled epsilon.  Squares below 2^-120 give up (hi = 1).
 __device__ __forceinline__ void eta_bounds(float a, float ea, bool za, float b, float eb, bool zb,
-                                           float tiny2, float &lo, float &hi)
+                                           float eps_hi, float &lo, float &hi)
 {
+    const float tiny = 7.52316385e-37f;                      // 2^-120
     if (za && zb) { lo = 1.0f; hi = 1.0f; return; }          // (0 + eps) / (0 + eps)
     if (za || zb) {                                           // eps / (d^2 + eps)
         const float d = za ? fabsf(b) - eb : fabsf(a) - ea;
         lo = 0.0f;
-        hi = (d > 0.0f && d * d >= tiny2) ? 1e-9f : 1.0f;
+        hi = (d > 0.0f && d * d >= tiny)
+                 ? fminf(__fdividef(eps_hi, d * d) * (1.0f + 1.0e-5f) + 1e-9f, 1.0f) : 1.0f;
         return;
     }
     const float al = fabsf(a) - ea, ah = fabsf(a) + ea;
@@ -147,7 +169,8 @@ __device__ __forceinline__ void eta_bounds(float a, float ea, bool za, float b, 
     const float e2 = __fdividef(2.0f * t2, 1.0f + t2 * t2);
     lo = fminf(e1, e2) * (1.0f - 1.0e-5f);
     float h = (t1 <= 1.0f && t2 >= 1.0f) ? 1.0f : fmaxf(e1, e2) * (1.0f + 1.0e-5f);
-    if (!(al * al + bl * bl >= tiny2)) h = 1.0f;             // eps may matter
+    const float D = al * al + bl * bl;
+    h = D >= tiny ? h + __fdividef(eps_hi, D) * (1.0f + 1.0e-5f) : 1.0f;
     hi = fminf(h + 1e-9f, 1.0f);
 }
 
@@ -246,27 +269,50 @@ __device__ __forceinline__ float pow7_sum2(float a, float b0, float b1, bool up)
     return (q0 * q0 * q0 * r0 + q1 * q1 * q1 * r1) * (up ? (1.0f + 2e-6f) : (1.0f - 2e-6f));
 }
 
+// Bounds of x = beta + eps from bounds lo <= beta <= hi (hi >= 0) and the
+// scaled epsilon's bounds with the factors 1 -+ 1e-6 already applied
+// (FastK::eb_lo, eb_hi): one rounding of the fma is covered by them.
+__device__ __forceinline__ float x_upper(float hi, float ehi)
+{
+    return fmaf(hi, 1.0f + 1.0e-6f, ehi);
+}
+__device__ __forceinline__ float x_lower(float lo, float elo)
+{
+    return fmaf(fmaxf(lo, 0.0f), 1.0f - 1.0e-6f, elo);
+}
+
 // Selection among the large stencils S_L, S_(L-1), ..., S_3, largest first:
 // chi_L >= C_T  <=>  sum_k (x_L / x_k)^7 <= 1/C_T - 1.  Accept when the upper
 // bound of the sum is at most thr, reject when its lower bound exceeds
-// thr_rej; x_L = beta_L + eps with the upper bound raised to tiny2 and the
-// lower bound required to reach it.  x0..x2 / X0..X2: lower / upper bounds of
-// the small stencils' x_k; lo, hi: the bounds of beta_L.  Returns L - 2 of
-// the accepted stencil, 0 when all are rejected, -1 when uncertain.
+// thr_rej; x_L = beta_L + eps, its lower bound required to reach tiny2 for
+// a rejection.  x0..x2 / X0..X2: lower / upper bounds of the small stencils'
+// x_k; lo, hi: the bounds of beta_L; elo, ehi: of the scaled epsilon.
+// Returns L - 2 of the accepted stencil, 0 when all are rejected, -1 when
+// uncertain.
 template <int H, int L>
 __device__ __forceinline__ int select_large(const float (&f)[2 * H], float lo, float hi, float tiny2,
-                                            float x0, float x1, float x2, float X0, float X1,
-                                            float X2, float thr, float thr_rej)
+                                            float elo, float ehi, float x0, float x1, float x2,
+                                            float X0, float X1, float X2, float thr, float thr_rej)
 {
-    if (pow7_sum(fmaxf(hi, tiny2), x0, x1, x2, true) <= thr) return L - 2;
-    if (!(lo >= tiny2) || !(pow7_sum(lo, X0, X1, X2, false) > thr_rej)) return -1;
+    if (pow7_sum(x_upper(hi, ehi), x0, x1, x2, true) <= thr) return L - 2;
+    const float xl = x_lower(lo, elo);
+    if (!(xl >= tiny2) || !(pow7_sum(xl, X0, X1, X2, false) > thr_rej)) return -1;
     if constexpr (L > 3) {
         float lo1, hi1;
         beta_large_bounds<H, L - 1>(f, lo1, hi1);
-        return select_large<H, L - 1>(f, lo1, hi1, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+        return select_large<H, L - 1>(f, lo1, hi1, tiny2, elo, ehi, x0, x1, x2, X0, X1, X2, thr,
+                                      thr_rej);
     } else {
         return 0;
     }
+}
+
+// A small indicator's FP64 input as the exact path forms it, converted to
+// scaled FP32 with the bound of its truncation and flush.
+__device__ __forceinline__ void small_in_exact(double x, int emax, float &v, float &err)
+{
+    v = d2f_scaled(x, emax);
+    err = 1.1920929e-7f * 1.0001f * fabsf(v) + 1.6e-30f;
 }
 
 // The filter.  v: the 2H values (FP64); s: shifted values s_m = v_m - v_0
@@ -303,9 +349,21 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     float f[W];
 #pragma unroll
     for (int j = 0; j < W; j++) f[j] = (j == H - 1) ? 0.0f : d2f_scaled(s[j], emax);
-    // indicator threshold 2^-100 in original units -> scaled units
-    const int tb = -100 - 2 * emax;
-    const float tiny2 = tb < -126 ? 1.17549435e-38f : __uint_as_float((unsigned)(tb + 127) << 23);
+    // floor of every x_k: 2^-140 in original units (the exact path's
+    // (beta+eps)^7 stays normal), at least 2^-120 scaled (FP32 stays normal)
+    const int tb = max(-140 - 2 * emax, -120);
+    const float tiny2 = __uint_as_float((unsigned)(tb + 127) << 23);
+    // the epsilons in scaled units, eps 2^-2emax = (eps 2^100) 2^(-2emax-100)
+    float ebl = 0.0f, ebh = 7.52316385e-37f, eeh = 7.52316385e-37f;   // 2^-120 bounds below
+    {
+        const int ke = -2 * emax - 100;
+        if (ke >= -90) {
+            const float pw = __uint_as_float((unsigned)(ke + 127) << 23);
+            ebl = F.eb_lo * pw;
+            ebh = F.eb_hi * pw;
+            eeh = F.ee_hi * pw;
+        }
+    }
     const float u23 = 1.1920929e-7f * 1.0001f, u24 = 5.9604645e-8f * 1.0001f;
     const float z100 = 1.6e-30f;             // > 2^-100: flushed-value error
     // The exact path evaluates the small indicators on the unshifted values:
@@ -319,38 +377,45 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const float eo = ev < -900 ? 0.0f : __uint_as_float((unsigned)(max(ev - emax - 50, -126) + 127) << 23);
 #define FF(m) f[(m) + H - 1]
 
-    // Small indicators on the shifted values (s_0 = 0).
+    // Inputs a_k, b_k of the three small indicators with absolute error
+    // bounds (scaled units).
+    float sa[3], sea[3], sb[3], seb[3];
+    if (ev - emax >= 30) {
+        // values within 2^-30 of one another relative to their size: the
+        // exact path's rounding on the unshifted values is then as large as
+        // their differences, so take its own FP64 inputs (the same
+        // operations: bitwise its values) and bound only their conversion
+        small_in_exact(VV(-1) - VV(1), emax, sa[0], sea[0]);
+        small_in_exact((VV(-1) - 2.0 * VV(0)) + VV(1), emax, sb[0], seb[0]);
+        small_in_exact((3.0 * VV(0) - 4.0 * VV(1)) + VV(2), emax, sa[1], sea[1]);
+        small_in_exact((VV(0) - 2.0 * VV(1)) + VV(2), emax, sb[1], seb[1]);
+        small_in_exact((VV(-2) - 4.0 * VV(-1)) + 3.0 * VV(0), emax, sa[2], sea[2]);
+        small_in_exact((VV(-2) - 2.0 * VV(-1)) + VV(0), emax, sb[2], seb[2]);
+    } else {
+        // on the shifted values (s_0 = 0); the slack holds the exact path's
+        // rounding on the unshifted values
+        const float sl0 = 2.0f * z100 + 4.0f * eo, sl1 = 5.0f * z100 + 8.0f * eo;
+        sa[0] = FF(-1) - FF(1);
+        sea[0] = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(sa[0]) + sl0;
+        sb[0] = FF(-1) + FF(1);
+        seb[0] = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(sb[0]) + sl0;
+        sa[1] = FF(2) - 4.0f * FF(1);
+        sea[1] = u23 * (fabsf(FF(2)) + 4.0f * fabsf(FF(1))) + u24 * fabsf(sa[1]) + sl1;
+        sb[1] = FF(2) - 2.0f * FF(1);
+        seb[1] = u23 * (fabsf(FF(2)) + 2.0f * fabsf(FF(1))) + u24 * fabsf(sb[1]) + sl1;
+        sa[2] = FF(-2) - 4.0f * FF(-1);
+        sea[2] = u23 * (fabsf(FF(-2)) + 4.0f * fabsf(FF(-1))) + u24 * fabsf(sa[2]) + sl1;
+        sb[2] = FF(-2) - 2.0f * FF(-1);
+        seb[2] = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(sb[2]) + sl1;
+    }
     float b0, e0, b1, e1, b2, e2;
-    {
-        const float slack = 2.0f * z100 + 4.0f * eo;
-        const float a = FF(-1) - FF(1);
-        const float ea = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(a) + slack;
-        const float b = FF(-1) + FF(1);
-        const float eb = u23 * (fabsf(FF(-1)) + fabsf(FF(1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b0, e0);
-    }
-    {
-        const float slack = 5.0f * z100 + 8.0f * eo;
-        const float a = FF(2) - 4.0f * FF(1);
-        const float ea = u23 * (fabsf(FF(2)) + 4.0f * fabsf(FF(1))) + u24 * fabsf(a) + slack;
-        const float b = FF(2) - 2.0f * FF(1);
-        const float eb = u23 * (fabsf(FF(2)) + 2.0f * fabsf(FF(1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b1, e1);
-    }
-    {
-        const float slack = 5.0f * z100 + 8.0f * eo;
-        const float a = FF(-2) - 4.0f * FF(-1);
-        const float ea = u23 * (fabsf(FF(-2)) + 4.0f * fabsf(FF(-1))) + u24 * fabsf(a) + slack;
-        const float b = FF(-2) - 2.0f * FF(-1);
-        const float eb = u23 * (fabsf(FF(-2)) + 2.0f * fabsf(FF(-1))) + u24 * fabsf(b) + slack;
-        small_beta(a, ea, b, eb, b2, e2);
-    }
-    // x_k = beta_k + eps: lower bounds (eps dropped) and upper bounds (eps
-    // < 1.3e-10 tiny2 <= 1.3e-10 x_k folded into the factor).
-    const float x0 = b0 - e0, x1 = b1 - e1, x2 = b2 - e2;
+    small_beta(sa[0], sea[0], sb[0], seb[0], b0, e0);
+    small_beta(sa[1], sea[1], sb[1], seb[1], b1, e1);
+    small_beta(sa[2], sea[2], sb[2], seb[2], b2, e2);
+    // x_k = beta_k + eps: lower and upper bounds, the lower ones at tiny2 or above
+    const float x0 = x_lower(b0 - e0, ebl), x1 = x_lower(b1 - e1, ebl), x2 = x_lower(b2 - e2, ebl);
     if (!(x0 >= tiny2) || !(x1 >= tiny2) || !(x2 >= tiny2)) return false;
-    const float X0 = (b0 + e0) * (1.0f + 1e-6f), X1 = (b1 + e1) * (1.0f + 1e-6f);
-    const float X2 = (b2 + e2) * (1.0f + 1e-6f);
+    const float X0 = x_upper(b0 + e0, ebh), X1 = x_upper(b1 + e1, ebh), X2 = x_upper(b2 + e2, ebh);
 
     // Without a decision record the exponent only matters when S_p is not
     // accepted: accept it at once when chi_p >= C_T holds for the largest
@@ -362,7 +427,7 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     if (!need_ct) {
         // sum_k (x_p / x_k)^7 <= 3 (x_p / min_k x_k)^7: one division for the
         // common case (a looser bound only sends borderline cases on)
-        const float r = __fdividef(fmaxf(bhi, tiny2), fminf(x0, fminf(x1, x2))) * (1.0f + 5e-7f);
+        const float r = __fdividef(x_upper(bhi, ebh), fminf(x0, fminf(x1, x2))) * (1.0f + 5e-7f);
         const float q = r * r;
         if (3.0f * (q * q * q * r) * (1.0f + 4e-6f) <= F.thr[F.nexp_min]) {
             flag = (uint8_t)large_code(H);
@@ -384,7 +449,7 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
 #pragma unroll
     for (int j = -1; j <= 2; j++) {
         float lo, hi;
-        eta_bounds(dl[j + 2], el[j + 2], zl[j + 2], dl[j + 1], el[j + 1], zl[j + 1], tiny2, lo, hi);
+        eta_bounds(dl[j + 2], el[j + 2], zl[j + 2], dl[j + 1], el[j + 1], zl[j + 1], eeh, lo, hi);
         emin_lo = fminf(emin_lo, lo);
         emin_hi = fminf(emin_hi, hi);
     }
@@ -410,7 +475,8 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const float thr = F.thr[nexp], thr_rej = F.thr_rej[nexp];
 
     // Targeted selection, largest group first (Sec. 3.3).
-    const int sel = select_large<H, H>(f, blo, bhi, tiny2, x0, x1, x2, X0, X1, X2, thr, thr_rej);
+    const int sel = select_large<H, H>(f, blo, bhi, tiny2, ebl, ebh, x0, x1, x2, X0, X1, X2, thr,
+                                       thr_rej);
     if (sel < 0) return false;
     if (sel > 0) {
         if constexpr (H == 6)

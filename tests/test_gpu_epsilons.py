@@ -1,7 +1,7 @@
 """Epsilons other than the paper's 1e-40 (Eq. scale_separation; the eta
 measure of Sec. 3.4).  The certified single-precision decision filter's
-error bounds treat both epsilons as negligible above 2^-100, which holds up
-to 1e-40; with larger ones the library takes every decision in FP64.  With
+error bounds carry both epsilons explicitly and are used up to 1e-40; with
+larger ones the library takes every decision in FP64.  With
 each epsilon pair the right-hand side and its decision record must be the
 same bit for bit with the filter switch on and off, and equal to the oracle
 run with the same epsilons.  The data are chosen so that 1e-6 changes many

@@ -279,3 +279,31 @@ def test_filter_whole_record_2d_1024():
     r_on, f_on, r_off, f_off = _rhs_both_ways(s, Ud)
     assert torch.equal(f_on, f_off)
     assert torch.equal(r_on, r_off)
+
+
+@pytest.mark.parametrize("scheme", [8, 10, 12])
+def test_filter_decides_noise_plateaus_2d(scheme):
+    """1024^2 four quadrants after 45 steps: rounding noise has then spread
+    over the constant states (the numerical domain of dependence grows by up
+    to 3H cells a step), and their decisions follow the noise.  The filter
+    must still decide all but a small share of the reconstructions (before
+    it handled such values it sent 95 % of them to the FP64 path), with the
+    decision record and the RHS identical to the FP64 path's."""
+    c = workloads.quadrants_2d(1024, scheme=scheme)
+    s = T.Solver(gpu_params(c))
+    Ud = torch.from_numpy(c["U"]).to(DEV)
+    for _ in range(45):
+        s.cfl_dt(Ud, 0.4)
+        s.step(Ud)
+    T.teno_profile_enable(True)
+    try:
+        s.rhs(Ud)
+        torch.cuda.synchronize()
+        _, _, faces, exact = T.teno_profile_read()
+    finally:
+        T.teno_profile_enable(False)
+    share = exact / (faces * 2 * 4)
+    assert share < 0.02, "exact-path share %.4f" % share
+    r_on, f_on, r_off, f_off = _rhs_both_ways(s, Ud)
+    assert torch.equal(f_on, f_off)
+    assert torch.equal(r_on, r_off)

@@ -162,9 +162,42 @@ def random_stencils(scheme, n=20000, seed=7):
     return np.array(V)
 
 
+def noise_stencils(scheme, n=6000, seed=11):
+    """Values that agree to within rounding, as in a plateau that rounding
+    noise has reached: O(1) values a few ulps apart (around powers of two
+    too, where the exact path's own rounding changes binade), the LLF
+    split's near-cancelling side (tiny values of either sign), and plateaus
+    exactly constant on part of the stencil (small indicators exactly 0)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    W = scheme
+    V = []
+    for i in range(n):
+        kind = i % 6
+        if kind in (0, 1):     # O(1) values, offsets of a few ulps
+            v0 = g.choice([-1.0, 1.0]) * 10.0 ** g.uniform(-6, 6)
+            if kind == 1:      # just below / above a power of two
+                v0 = np.ldexp(1.0, int(g.integers(-20, 20))) * (1.0 + g.choice([-1, 1]) * 2.0 ** -50)
+            k = g.integers(-3, 4, W).astype(float)
+            v = v0 + k * np.spacing(v0)
+        elif kind == 2:        # tiny values of either sign
+            v = g.standard_normal(W) * 10.0 ** g.uniform(-30, -8)
+        elif kind == 3:        # tiny multiples of one ulp-sized unit
+            v = g.integers(-4, 5, W).astype(float) * 10.0 ** g.uniform(-24, -12)
+        elif kind == 4:        # exactly constant run, then a few ulps of noise
+            v0 = 10.0 ** g.uniform(-3, 3)
+            v = np.full(W, v0)
+            j = g.integers(1, W)
+            v[j:] += g.integers(-2, 3, W - j) * np.spacing(v0)
+        else:                  # noise about a value with a large-ish exponent spread
+            v0 = 10.0 ** g.uniform(-2, 2)
+            v = v0 * (1.0 + g.standard_normal(W) * 10.0 ** g.uniform(-15, -9))
+        V.append(v)
+    return np.array(V)
+
+
 @pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_reconstruction_matches_oracle(scheme):
-    V = np.concatenate([random_stencils(scheme), adversarial(scheme)])
+    V = np.concatenate([random_stencils(scheme), adversarial(scheme), noise_stencils(scheme)])
     ref, rfl = oracle_batch(scheme, V)
     for fast in (True, False):
         out, fl = gpu_batch(scheme, V, fast)

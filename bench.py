@@ -538,7 +538,7 @@ def run_adjoint(args, dev, stream):
     for _ in range(nsteps):
         U1, U2 = torch.empty_like(U), torch.empty_like(U)
         fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
-        T.teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
+        T.teno_rk3_step_record_sel(p, U, dt, U1, U2, fl, fws)
         fls.append(fl)
         del U1, U2
     e4.record(stream)

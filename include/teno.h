@@ -279,6 +279,17 @@ int teno_rhs_vjp(const teno_params *p, const double *U, const double *lam, const
 int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
                          uint8_t *flags, void *ws, size_t ws_bytes, void *stream);
 
+/* teno_rk3_step_record with a selection-only record: the same U^{n+1}, U1,
+ * U2, argmax words and limiter bytes, and decision bytes whose selection and
+ * cut-off bits (0-4) are those of the full record, while the C_T exponent
+ * bits (5-7) are set only where the exponent was needed to decide and are 0
+ * where the certified filter accepted S_p for every exponent the parameters
+ * allow (it then skips the eta measure of Sec. 3.4).  The adjoint calls read
+ * bits 0-4 and the argmax words only, so this record serves them at the
+ * cost of a plain step; rollout() records with it. */
+int teno_rk3_step_record_sel(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                             uint8_t *flags, void *ws, size_t ws_bytes, void *stream);
+
 /* The frozen-decision map whose derivative the adjoint applies: L(U) (and one
  * SSP-RK3 step) with every reconstruction taken from the recorded decision
  * bytes (one teno_flags_bytes block for teno_rhs_frozen; three, one per

@@ -97,6 +97,7 @@ def load():
         lib.teno_adjoint_workspace_bytes.argtypes = [P, ctypes.POINTER(sz)]
         lib.teno_rhs_vjp.argtypes = [P, vp, vp, vp, vp, vp, sz, vp]
         lib.teno_rk3_step_record.argtypes = [P, vp, ctypes.c_double, vp, vp, u8p, vp, sz, vp]
+        lib.teno_rk3_step_record_sel.argtypes = [P, vp, ctypes.c_double, vp, vp, u8p, vp, sz, vp]
         lib.teno_rk3_step_vjp.argtypes = [P, vp, vp, vp, u8p, ctypes.c_double, vp, vp, sz, vp]
         lib.teno_rhs_frozen.argtypes = [P, vp, vp, ctypes.c_double, u8p, vp, sz, vp]
         lib.teno_rk3_step_frozen.argtypes = [P, vp, ctypes.c_double, u8p, vp, sz, vp]
@@ -127,8 +128,8 @@ def load():
                      "teno_profile_read", "teno_set_decision_filter", "teno_reconstruct", "teno_rhs_static", "teno_batch_create",
                      "teno_batch_workspace_bytes", "teno_batch_autotune", "teno_batch_rk3_steps",
                      "teno_batch_times", "teno_adjoint_workspace_bytes", "teno_rhs_vjp",
-                     "teno_rk3_step_record", "teno_rk3_step_vjp", "teno_rhs_frozen",
-                     "teno_rk3_step_frozen", "teno_rk3_stage", "teno_wave_speeds",
+                     "teno_rk3_step_record", "teno_rk3_step_record_sel", "teno_rk3_step_vjp",
+                     "teno_rhs_frozen", "teno_rk3_step_frozen", "teno_rk3_stage", "teno_wave_speeds",
                      "teno_dt_from_speeds", "teno_debug_bounds", "teno_build_flags"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -142,7 +143,7 @@ EXPORTS = ("teno_params_init", "teno_workspace_bytes", "teno_flags_bytes", "teno
            "teno_batch_create", "teno_batch_workspace_bytes", "teno_batch_autotune",
            "teno_batch_rk3_steps", "teno_batch_times", "teno_batch_destroy",
            "teno_adjoint_workspace_bytes", "teno_rhs_vjp", "teno_rk3_step_record",
-           "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen",
+           "teno_rk3_step_record_sel", "teno_rk3_step_vjp", "teno_rhs_frozen", "teno_rk3_step_frozen",
            "teno_rk3_stage", "teno_wave_speeds", "teno_dt_from_speeds", "teno_debug_bounds",
            "teno_build_flags")
 
@@ -640,6 +641,16 @@ def teno_rk3_step_record(p, U, dt, U1, U2, flags, ws, stream=None):
                                        _stream(stream)), "teno_rk3_step_record")
 
 
+def teno_rk3_step_record_sel(p, U, dt, U1, U2, flags, ws, stream=None):
+    """teno_rk3_step_record whose decision bytes carry the C_T exponent only
+    where it was needed (the selection bits, argmax words and states are
+    the full record's)."""
+    _check(load().teno_rk3_step_record_sel(ctypes.byref(p), _ptr(U), float(dt), _ptr(U1),
+                                           _ptr(U2), _ptr(flags), _ptr(ws),
+                                           ws.numel() * ws.element_size(), _stream(stream)),
+           "teno_rk3_step_record_sel")
+
+
 def teno_rhs_frozen(p, U, rhs, decisions, ws, dt_limiter=0.0, stream=None):
     _check(load().teno_rhs_frozen(ctypes.byref(p), _ptr(U), _ptr(rhs), float(dt_limiter),
                                   _ptr(decisions), _ptr(ws), ws.numel() * ws.element_size(),
@@ -665,9 +676,9 @@ def _rollout_class():
     class TenoRollout(torch.autograd.Function):
         """nsteps SSP-RK3 steps at a fixed dt; the backward walks checkpoint
         segments in reverse: recompute the segment's steps keeping stage
-        states and decision records (the last segment's are kept from the
-        forward), then apply teno_rk3_step_vjp step by step (decisions frozen
-        as in the forward)."""
+        states and selection-only decision records (the last segment's are
+        kept from the forward), then apply teno_rk3_step_vjp step by step
+        (decisions frozen as in the forward)."""
 
         @staticmethod
         def forward(ctx, U0, p, dt, nsteps, every):
@@ -687,7 +698,7 @@ def _rollout_class():
                 if k >= last:
                     Un, U1, U2 = U.clone(), torch.empty_like(U), torch.empty_like(U)
                     fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
-                    teno_rk3_step_record(p, U, float(dt), U1, U2, fl, ws)
+                    teno_rk3_step_record_sel(p, U, float(dt), U1, U2, fl, ws)
                     rec.append((Un, U1, U2, fl))
                 else:
                     teno_rk3_step(p, U, float(dt), None, ws)
@@ -718,7 +729,7 @@ def _rollout_class():
                         U1 = torch.empty_like(U)
                         U2 = torch.empty_like(U)
                         fl = torch.empty(3 * flb, dtype=torch.uint8, device=dev)
-                        teno_rk3_step_record(p, U, dt, U1, U2, fl, fws)
+                        teno_rk3_step_record_sel(p, U, dt, U1, U2, fl, fws)
                         rec.append((Un, U1, U2, fl))
                 for Un, U1, U2, fl in reversed(rec):
                     teno_rk3_step_vjp(p, Un, U1, U2, fl, dt, abar, aws)

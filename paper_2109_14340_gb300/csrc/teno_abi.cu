@@ -447,9 +447,11 @@ static cudaError_t profile_mark(int which, int slot, cudaStream_t s)
 // sweeps, or nullptr (the sweeps compute them and the x sweep counts the
 // non-physical cells); P_out: where the combine stores the primitives of
 // its output for the next stage, or nullptr.
+// full_ct = false: a recorded decision byte carries its C_T exponent only
+// where the exponent was needed to decide (the selection-only record).
 static int stage(const teno_params *p, const double *Uk, const double *Un, double *out, int mode,
                  double dt_host, const double *dt_dev, uint8_t *flags, char *ws, cudaStream_t s,
-                 const uint8_t *frozen, const double *P_in, double *P_out)
+                 const uint8_t *frozen, const double *P_in, double *P_out, bool full_ct = true)
 {
     static const char *kStageName[4] = {"teno rhs", "teno rk3 stage 1", "teno rk3 stage 2",
                                         "teno rk3 stage 3"};
@@ -495,6 +497,7 @@ static int stage(const teno_params *p, const double *Uk, const double *Un, doubl
         a.bcs_hi = p->bc_state_hi[d];
         a.lam = &st->lam[d];
         a.fast = filter_on(p);
+        a.need_ct = (fl && full_ct) ? 1 : 0;
         a.skip_last = (p->bc_lo[d] == TENO_BC_PERIODIC && !fl && !fz) ? 1 : 0;
         a.count_cells = (d == 0 && !P_in);        // the x sweep counts the stage input's cells
                                                   // unless its primitives were stored
@@ -627,8 +630,8 @@ int teno_rk3_step(const teno_params *p, double *U, double dt, const double *dt_d
     return stage(p, Us, U, U, 3, dt, dt_device, nullptr, (char *)ws, s, nullptr, P, nullptr);
 }
 
-int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
-                         uint8_t *flags, void *ws, size_t ws_bytes, void *stream)
+static int rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                           uint8_t *flags, void *ws, size_t ws_bytes, void *stream, bool full_ct)
 {
     int r = validate(p);
     if (r) return r;
@@ -640,9 +643,24 @@ int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1,
     // the stages of teno_rk3_step, with the stage states and decision records kept
     double *P = nullptr;
     CUDA_TRY(launch_prims(p, U, (char *)ws, s, &P));
-    if ((r = stage(p, U, U, U1, 1, dt, nullptr, flags, (char *)ws, s, nullptr, P, P))) return r;
-    if ((r = stage(p, U1, U, U2, 2, dt, nullptr, flags + flb, (char *)ws, s, nullptr, P, P))) return r;
-    return stage(p, U2, U, U, 3, dt, nullptr, flags + 2 * flb, (char *)ws, s, nullptr, P, nullptr);
+    if ((r = stage(p, U, U, U1, 1, dt, nullptr, flags, (char *)ws, s, nullptr, P, P, full_ct)))
+        return r;
+    if ((r = stage(p, U1, U, U2, 2, dt, nullptr, flags + flb, (char *)ws, s, nullptr, P, P, full_ct)))
+        return r;
+    return stage(p, U2, U, U, 3, dt, nullptr, flags + 2 * flb, (char *)ws, s, nullptr, P, nullptr,
+                 full_ct);
+}
+
+int teno_rk3_step_record(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                         uint8_t *flags, void *ws, size_t ws_bytes, void *stream)
+{
+    return rk3_step_record(p, U, dt, U1, U2, flags, ws, ws_bytes, stream, true);
+}
+
+int teno_rk3_step_record_sel(const teno_params *p, double *U, double dt, double *U1, double *U2,
+                             uint8_t *flags, void *ws, size_t ws_bytes, void *stream)
+{
+    return rk3_step_record(p, U, dt, U1, U2, flags, ws, ws_bytes, stream, false);
 }
 
 int teno_rhs_frozen(const teno_params *p, const double *U, double *rhs, double dt_limiter,

@@ -273,7 +273,17 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
     double alphab[nc];
 
     // A shear field's row of L is (-u_t, e_t, 0): only its columns 0 and
-    // 1 + t enter the sums below (branches uniform over the warp).
+    // 1 + t enter the products below (branches uniform over the warp).
+    // With P_j = (c+_j + c-_j)/2 and Q_j = (c+_j - c-_j)/2 the frozen
+    // reconstruction gives h_k = alpha sum_j Q_j w_j + sum_j P_j g_j; with
+    // A_c = sum_j Q_j U_cj and B_c = sum_j P_j F_cj (w = l.U, g = l.F):
+    // sum_j Q_j w_j = l.A, h_k = alpha l.A + l.B, and the adjoint of the
+    // row l is hb_k (alpha A + B).  A and B depend on the field only through
+    // its two decision bytes' low five bits (the frozen coefficients), so
+    // they are formed again only when those change from the previous field
+    // (in smooth regions every field has the same selection).
+    double A[nc], B[nc];
+    int abkey = -1;
 #pragma unroll 1
     for (int k = 0; k < nc; k++) {
         const bool shear = (k >= 2 && k < last);
@@ -293,28 +303,26 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
             if (k == kk) hbk = hb[kk];
         const double alpha = a.K.split ? ar : (k == 0 ? am : (k == last ? ap : a0));
         const uint8_t flp = fl[2 * k], flm = fl[2 * k + 1];
-        // With P_j = (c+_j + c-_j)/2 and Q_j = (c+_j - c-_j)/2 the frozen
-        // reconstruction gives h_k = alpha sum_j Q_j w_j + sum_j P_j g_j; with
-        // A_c = sum_j Q_j U_cj and B_c = sum_j P_j F_cj (w = l.U, g = l.F):
-        // sum_j Q_j w_j = l.A, h_k = alpha l.A + l.B, and the adjoint of the
-        // row l is hb_k (alpha A + B).
-        double A[nc], B[nc];           // accumulated with 2 Q_j, 2 P_j, halved after
+        const int key = (flp & 31) | ((flm & 31) << 5);
+        if (key != abkey) {
+            // accumulated with 2 Q_j, 2 P_j, halved after
 #pragma unroll
-        for (int c = 0; c < nc; c++) { A[c] = 0.0; B[c] = 0.0; }
+            for (int c = 0; c < nc; c++) { A[c] = 0.0; B[c] = 0.0; }
 #pragma unroll
-        for (int j = 0; j < W; j++) {
-            const double cp = frozen_coef<H>(flp, j);          // v+ index j <-> cell j
-            const double cm = frozen_coef<H>(flm, W - 1 - j);  // v- index W-1-j <-> cell j
-            const double Pc = cp + cm, Qc = cp - cm;
+            for (int j = 0; j < W; j++) {
+                const double cp = frozen_coef<H>(flp, j);          // v+ index j <-> cell j
+                const double cm = frozen_coef<H>(flm, W - 1 - j);  // v- index W-1-j <-> cell j
+                const double Pc = cp + cm, Qc = cp - cm;
 #pragma unroll
-            for (int c = 0; c < nc; c++) {
-                if (shear && c != 0 && c != 1 + tk) continue;
-                A[c] = fma(Qc, SQ(SL::QU + c, fo + j, p), A[c]);
-                B[c] = fma(Pc, SQ(SL::QF + c, fo + j, p), B[c]);
+                for (int c = 0; c < nc; c++) {
+                    A[c] = fma(Qc, SQ(SL::QU + c, fo + j, p), A[c]);
+                    B[c] = fma(Pc, SQ(SL::QF + c, fo + j, p), B[c]);
+                }
             }
-        }
 #pragma unroll
-        for (int c = 0; c < nc; c++) { A[c] *= 0.5; B[c] *= 0.5; }
+            for (int c = 0; c < nc; c++) { A[c] *= 0.5; B[c] *= 0.5; }
+            abkey = key;
+        }
         double wq = lrow[0] * A[0], gp = lrow[0] * B[0];
 #pragma unroll
         for (int c = 1; c < nc; c++) {
@@ -572,10 +580,54 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
 // ghost image) of their slot adjoints; the flux part goes through the flux
 // Jacobian's transpose at the (ghost) state, slip-wall images through the
 // mirror.
+// Sum of the slots of the faces whose stencils cover position g along D
+// (a cell or one of its ghost images) at the transverse position (x, y, z):
+// face f holds position g at stencil index j = g - f + H.  A position whose
+// 2H faces all exist (the interior) takes an unrolled loop, so that its 4 H
+// nc loads are independent.
+template <int ND, int H, int D>
+__device__ __forceinline__ void gather_position(const AdjArgs &a, int64_t g, int64_t x, int64_t y,
+                                                int64_t z, double (&Us)[ND + 2],
+                                                double (&Fm)[ND + 2])
+{
+    constexpr int nc = ND + 2, W = 2 * H;
+    const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
+    // linear face index = fb + f * fs
+    int64_t fb, fs;
+    if (D == 0) { fb = (n0 + 1) * (y + n1 * z); fs = 1; }
+    else if (D == 1) { fb = x + n0 * (n1 + 1) * z; fs = n0; }
+    else { fb = x + n0 * y; fs = n0 * n1; }
+#pragma unroll
+    for (int c = 0; c < nc; c++) { Us[c] = 0.0; Fm[c] = 0.0; }
+    if (g - H + 1 >= 0 && g + H <= nD) {
+#pragma unroll
+        for (int t = 0; t < W; t++) {
+            const int64_t f = g - H + 1 + t;
+            const double *sl = a.slots + (size_t)(W - 1 - t) * 2 * nc * a.nfaces + fb + f * fs;
+#pragma unroll
+            for (int c = 0; c < nc; c++) {
+                Us[c] += sl[c * a.nfaces];
+                Fm[c] += sl[(nc + c) * a.nfaces];
+            }
+        }
+    } else {
+        const int64_t flo = g - H + 1 > 0 ? g - H + 1 : 0;
+        const int64_t fhi = g + H < nD ? g + H : nD;
+        for (int64_t f = flo; f <= fhi; f++) {
+            const double *sl = a.slots + (size_t)(g - f + H) * 2 * nc * a.nfaces + fb + f * fs;
+#pragma unroll
+            for (int c = 0; c < nc; c++) {
+                Us[c] += sl[c * a.nfaces];
+                Fm[c] += sl[(nc + c) * a.nfaces];
+            }
+        }
+    }
+}
+
 template <int ND, int H, int D>
 __global__ void adj_gather_kernel(AdjArgs a, double *mu, int accumulate)
 {
-    constexpr int nc = ND + 2, W = 2 * H;
+    constexpr int nc = ND + 2;
     const int64_t n0 = a.n[0], n1 = a.n[1], nD = a.n[D];
     for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < a.ncell;
          id += (int64_t)gridDim.x * blockDim.x) {
@@ -584,60 +636,45 @@ __global__ void adj_gather_kernel(AdjArgs a, double *mu, int accumulate)
         double Uc[nc];
 #pragma unroll
         for (int c = 0; c < nc; c++) Uc[c] = a.U[c * a.ncell + id];
+        // the cell itself
         double Ut[nc], Fs[nc];
-#pragma unroll
-        for (int c = 0; c < nc; c++) { Ut[c] = 0.0; Fs[c] = 0.0; }
-        // candidate positions g along D that map to cell i, with the mirror
-        // rule of their image (0 none, 1 slip wall, 2 no-slip)
-        int64_t gs[2 * 5 + 3];
-        int ms[2 * 5 + 3];
-        int ng = 0;
-        gs[ng] = i; ms[ng] = 0; ng++;
-        if (a.bc_lo == 0) { gs[ng] = i - nD; ms[ng] = 0; ng++; }
-        if (a.bc_hi == 0) { gs[ng] = i + nD; ms[ng] = 0; ng++; }
-        if (a.bc_lo == 1 && i == 0)
-            for (int r = 1; r <= H; r++) { gs[ng] = -r; ms[ng] = 0; ng++; }
-        if (a.bc_hi == 1 && i == nD - 1)
-            for (int r = 0; r < H; r++) { gs[ng] = nD + r; ms[ng] = 0; ng++; }
-        if ((a.bc_lo == 2 || a.bc_lo == 3) && i < H) { gs[ng] = -i - 1; ms[ng] = a.bc_lo - 1; ng++; }
-        if ((a.bc_hi == 2 || a.bc_hi == 3) && i >= nD - H) {
-            gs[ng] = 2 * nD - 1 - i; ms[ng] = a.bc_hi - 1; ng++;
-        }
-        for (int q = 0; q < ng; q++) {
-            const int64_t g = gs[q];
-            if (g < -H || g > nD + H - 1) continue;
-            double Us[nc], Fm[nc];
-#pragma unroll
-            for (int c = 0; c < nc; c++) { Us[c] = 0.0; Fm[c] = 0.0; }
-            const int64_t flo = g - H + 1 > 0 ? g - H + 1 : 0;
-            const int64_t fhi = g + H < nD ? g + H : nD;
-            for (int64_t f = flo; f <= fhi; f++) {
-                const int j = (int)(g - f + H);
-                int64_t flin;
-                if (D == 0) flin = f + (n0 + 1) * (y + n1 * z);
-                else if (D == 1) flin = x + n0 * (f + (n1 + 1) * z);
-                else flin = x + n0 * (y + n1 * f);
-                const double *sl = a.slots + (size_t)j * 2 * nc * a.nfaces + flin;
-#pragma unroll
-                for (int c = 0; c < nc; c++) {
-                    Us[c] += sl[c * a.nfaces];
-                    Fm[c] += sl[(nc + c) * a.nfaces];
-                }
+        gather_position<ND, H, D>(a, i, x, y, z, Ut, Fs);
+        if (i < H || i >= nD - H) {
+            // ghost images that map to cell i, with the mirror rule of each
+            // image (0 none, 1 slip wall, 2 no-slip)
+            int64_t gs[2 * 5 + 2];
+            int ms[2 * 5 + 2];
+            int ng = 0;
+            if (a.bc_lo == 0) { gs[ng] = i - nD; ms[ng] = 0; ng++; }
+            if (a.bc_hi == 0) { gs[ng] = i + nD; ms[ng] = 0; ng++; }
+            if (a.bc_lo == 1 && i == 0)
+                for (int r = 1; r <= H; r++) { gs[ng] = -r; ms[ng] = 0; ng++; }
+            if (a.bc_hi == 1 && i == nD - 1)
+                for (int r = 0; r < H; r++) { gs[ng] = nD + r; ms[ng] = 0; ng++; }
+            if ((a.bc_lo == 2 || a.bc_lo == 3) && i < H) { gs[ng] = -i - 1; ms[ng] = a.bc_lo - 1; ng++; }
+            if ((a.bc_hi == 2 || a.bc_hi == 3) && i >= nD - H) {
+                gs[ng] = 2 * nD - 1 - i; ms[ng] = a.bc_hi - 1; ng++;
             }
-            if (!ms[q]) {
+            for (int q = 0; q < ng; q++) {
+                const int64_t g = gs[q];
+                if (g < -H || g > nD + H - 1) continue;
+                double Us[nc], Fm[nc];
+                gather_position<ND, H, D>(a, g, x, y, z, Us, Fm);
+                if (!ms[q]) {
 #pragma unroll
-                for (int c = 0; c < nc; c++) { Ut[c] += Us[c]; Fs[c] += Fm[c]; }
-            } else {
-                // the image is the mirror map M U (M diagonal, +-1): its flux
-                // Jacobian is taken at M U and M^T = M maps the adjoint back
-                double Ug[nc], Ub[nc];
+                    for (int c = 0; c < nc; c++) { Ut[c] += Us[c]; Fs[c] += Fm[c]; }
+                } else {
+                    // the image is the mirror map M U (M diagonal, +-1): its flux
+                    // Jacobian is taken at M U and M^T = M maps the adjoint back
+                    double Ug[nc], Ub[nc];
 #pragma unroll
-                for (int c = 0; c < nc; c++) { Ug[c] = Uc[c]; Ub[c] = Us[c]; }
-                apply_ghost_rule<ND, D>(Ug, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
-                flux_adjoint<ND, D>(Ug, Fm, a.K.gm1, Ub);
-                apply_ghost_rule<ND, D>(Ub, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
+                    for (int c = 0; c < nc; c++) { Ug[c] = Uc[c]; Ub[c] = Us[c]; }
+                    apply_ghost_rule<ND, D>(Ug, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
+                    flux_adjoint<ND, D>(Ug, Fm, a.K.gm1, Ub);
+                    apply_ghost_rule<ND, D>(Ub, ms[q], nullptr, nullptr, 0, 0, a.K.gm1);
 #pragma unroll
-                for (int c = 0; c < nc; c++) Ut[c] += Ub[c];
+                    for (int c = 0; c < nc; c++) Ut[c] += Ub[c];
+                }
             }
         }
         flux_adjoint<ND, D>(Uc, Fs, a.K.gm1, Ut);

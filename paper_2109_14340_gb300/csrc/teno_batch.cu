@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         a.bcs_hi = nullptr;
         a.lam = &slots[p].lam;
         a.fast = fast;
+        a.need_ct = 0;
         a.skip_last = 0;
         a.count_cells = 0;
         a.exact_count = nullptr;

@@ -36,6 +36,8 @@ struct FaceArgs {
                                      // axis D, or nullptr
     const double *lam;     // limiter's effective dt/dx for this direction (device)
     int fast;              // 1: certified FP32 decision filter first
+    int need_ct;           // 1: recorded decision bytes carry their C_T exponent; 0: only
+                           // where it decided (the selection bits are exact either way)
     int count_cells;       // 1: count the non-physical cells this sweep owns (one
                            // sweep per evaluation does, so each cell is counted once)
     int skip_last;         // 1: face n of each line is not computed (periodic axis, no
@@ -368,7 +370,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
-                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl, a.flags != nullptr);
+                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl, a.need_ct != 0);
                 // the largest stencil accepted (S6 as bits 0-4 zero).  Kept
                 // inline: the same test through a helper function made the 8-
                 // and 10-point sweeps 4-14 % slower (same registers, other code).

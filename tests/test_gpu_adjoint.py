@@ -193,6 +193,45 @@ def test_rk3_record_matches_step_and_vjp_dot():
     assert checked >= 1
 
 
+@pytest.mark.parametrize("nd", [2, 3])
+def test_selection_only_record(nd):
+    """teno_rk3_step_record_sel: the same step, stage states, argmax words and
+    limiter bytes as teno_rk3_step_record, and decision bytes whose low five
+    bits (all the adjoint reads) are the full record's; the C_T exponent bits
+    are the full record's or zero."""
+    if nd == 2:
+        c = workloads.adjoint_2d(40, 32)
+        scheme = 8
+    else:
+        c = workloads.tgv_3d(16, scheme=10)
+        scheme = 10
+    p = T.teno_params_init(ndim=nd, n=c["n"], dx=c["dx"], scheme=scheme, bc_lo=c["bc_lo"],
+                           bc_hi=c["bc_hi"])
+    dt, _, _ = oracle.cfl_dt(oracle_params(c), c["U"], 0.4)
+    fws = T.aligned_workspace(T.teno_workspace_bytes(p), DEV)
+    flb = T.teno_flags_bytes(p)
+    ndec, tot = _decision_parts(p)
+    outs = []
+    for rec in (T.teno_rk3_step_record, T.teno_rk3_step_record_sel):
+        U = torch.from_numpy(c["U"]).to(DEV)
+        U1, U2 = torch.empty_like(U), torch.empty_like(U)
+        fl = torch.empty(3 * flb, dtype=torch.uint8, device=DEV)
+        rec(p, U, dt, U1, U2, fl, fws)
+        outs.append((U, U1, U2, fl.cpu().numpy()))
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert torch.equal(a, b)
+    fa, fb = outs[0][3], outs[1][3]
+    zero_ct = 0
+    for s in range(3):
+        x, y = fa[s * tot:(s + 1) * tot], fb[s * tot:(s + 1) * tot]
+        assert np.array_equal(x[ndec:], y[ndec:])
+        assert np.array_equal(x[:ndec] & 0x1F, y[:ndec] & 0x1F)
+        ct_x, ct_y = x[:ndec] >> 5, y[:ndec] >> 5
+        assert np.all((ct_y == ct_x) | (ct_y == 0))
+        zero_ct += int(np.count_nonzero(ct_y != ct_x))
+    assert zero_ct > 0          # the quick acceptance did skip exponents
+
+
 def _decision_parts(p):
     """(bytes of the per-face decision bytes, total bytes) of one record."""
     nc = p.ndim + 2

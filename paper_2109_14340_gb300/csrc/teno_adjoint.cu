@@ -498,30 +498,67 @@ __global__ void __launch_bounds__(TP * TF) adj_face_kernel(AdjArgs a)
         sg[k] = 0.5 * hb[k];
         sw[k] = alpha * sg[k];
     }
-#pragma unroll 1
-    for (int j = 0; j < W; j++) {
-        double Ub[nc], Fcb[nc];
+    // Every field with the same frozen coefficients (each sign's decision
+    // bytes agree in their low five bits across the fields, as in smooth
+    // regions): the sums over the fields factor out of the stencil loop,
+    // Ub_c(j) = (c+_j - c-_j) sum_k L_kc sw_k and Fcb_c(j) = (c+_j + c-_j)
+    // sum_k L_kc sg_k.
+    bool uniform = true;
 #pragma unroll
-        for (int c = 0; c < nc; c++) { Ub[c] = 0.0; Fcb[c] = 0.0; }
+    for (int k = 1; k < nc; k++)
+        uniform = uniform && ((fl[2 * k] ^ fl[0]) & 31) == 0 && ((fl[2 * k + 1] ^ fl[1]) & 31) == 0;
+    if (uniform) {
+        double M[nc], N[nc];
+#pragma unroll
+        for (int c = 0; c < nc; c++) { M[c] = 0.0; N[c] = 0.0; }
 #pragma unroll
         for (int k = 0; k < nc; k++) {
-            const double cp = frozen_coef<H>(fl[2 * k], j);
-            const double cm = frozen_coef<H>(fl[2 * k + 1], W - 1 - j);
-            const double wb = sw[k] * (cp - cm);
-            const double gb = sg[k] * (cp + cm);
             const bool shear = (k >= 2 && k < last);
             const int tk = shear ? shear_axis<ND, D>(k) : 0;
 #pragma unroll
             for (int c = 0; c < nc; c++) {
                 if (shear && c != 0 && c != 1 + tk) continue;    // zeros of a shear row
-                Ub[c] = fma(Lm[k][c], wb, Ub[c]);
-                Fcb[c] = fma(Lm[k][c], gb, Fcb[c]);
+                M[c] = fma(Lm[k][c], sw[k], M[c]);
+                N[c] = fma(Lm[k][c], sg[k], N[c]);
             }
         }
+#pragma unroll 1
+        for (int j = 0; j < W; j++) {
+            const double cp = frozen_coef<H>(fl[0], j);
+            const double cm = frozen_coef<H>(fl[1], W - 1 - j);
+            const double qd = cp - cm, qs = cp + cm;
 #pragma unroll
-        for (int c = 0; c < nc; c++) {
-            out[(j * 2 * nc + c) * fs] = Ub[c];
-            out[(j * 2 * nc + nc + c) * fs] = Fcb[c];
+            for (int c = 0; c < nc; c++) {
+                out[(j * 2 * nc + c) * fs] = qd * M[c];
+                out[(j * 2 * nc + nc + c) * fs] = qs * N[c];
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int j = 0; j < W; j++) {
+            double Ub[nc], Fcb[nc];
+#pragma unroll
+            for (int c = 0; c < nc; c++) { Ub[c] = 0.0; Fcb[c] = 0.0; }
+#pragma unroll
+            for (int k = 0; k < nc; k++) {
+                const double cp = frozen_coef<H>(fl[2 * k], j);
+                const double cm = frozen_coef<H>(fl[2 * k + 1], W - 1 - j);
+                const double wb = sw[k] * (cp - cm);
+                const double gb = sg[k] * (cp + cm);
+                const bool shear = (k >= 2 && k < last);
+                const int tk = shear ? shear_axis<ND, D>(k) : 0;
+#pragma unroll
+                for (int c = 0; c < nc; c++) {
+                    if (shear && c != 0 && c != 1 + tk) continue;    // zeros of a shear row
+                    Ub[c] = fma(Lm[k][c], wb, Ub[c]);
+                    Fcb[c] = fma(Lm[k][c], gb, Fcb[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < nc; c++) {
+                out[(j * 2 * nc + c) * fs] = Ub[c];
+                out[(j * 2 * nc + nc + c) * fs] = Fcb[c];
+            }
         }
     }
 

@@ -322,7 +322,9 @@ def fallback_weights():
     for mask in range(8):
         dd = [d[k] if mask >> k & 1 else 0.0 for k in range(3)]
         den = (dd[0] + dd[1]) + dd[2]
-        rows.append([x / den for x in dd] if den else [0.0, 0.0, 0.0])
+        # no candidate kept (every cut-off failed, possible only for C_T = 1):
+        # Eq. renormalize is 0/0, NaN as its literal evaluation gives
+        rows.append([x / den for x in dd] if den else [float("nan")] * 3)
     return rows
 
 
@@ -338,12 +340,19 @@ def fallback_table():
         dd = [d[k] if mask >> k & 1 else 0.0 for k in range(3)]
         den = (dd[0] + dd[1]) + dd[2]
         if den == 0.0:
-            rows.append([0.0] * 5)       # no candidate kept: cannot occur
+            rows.append([float("nan")] * 5)     # no candidate kept: 0/0 weights
             continue
         w0, w1, w2 = dd[0] / den, dd[1] / den, dd[2] / den
         rows.append([2.0 * w2 / 6.0, (-w0 - 7.0 * w2) / 6.0, (5.0 * w0 + 2.0 * w1 + 11.0 * w2) / 6.0,
                      (2.0 * w0 + 5.0 * w1) / 6.0, -w1 / 6.0])
     return rows
+
+
+def _c(x):
+    """A double as a C literal (hexadecimal, NaN as the compiler builtin)."""
+    if x != x:
+        return '__builtin_nan("")'
+    return float.hex(x) if x else "0.0"
 
 
 def emit():
@@ -371,16 +380,17 @@ def emit():
     out.append("")
     out.append("static __constant__ double TENO_DK[3] = {%s};" % ", ".join(DK))
     out.append("// Renormalised fallback weights w_k = d_k delta_k / sum_j d_j delta_j (double")
-    out.append("// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index.")
+    out.append("// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index;")
+    out.append("// NaN (0/0) when no candidate is kept.")
     out.append("static __constant__ double TENO_FBW[8][3] = {")
     for r in fallback_weights():
-        out.append("    {" + ", ".join(float.hex(x) if x else "0.0" for x in r) + "},")
+        out.append("    {" + ", ".join(_c(x) for x in r) + "},")
     out.append("};")
     out.append("// Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,")
     out.append("// delta_2) = bits 0..2 of the row index.")
     out.append("static __constant__ double TENO_FBK[8][5] = {")
     for r in fallback_table():
-        out.append("    {" + ", ".join(float.hex(x) if x else "0.0" for x in r) + "},")
+        out.append("    {" + ", ".join(_c(x) for x in r) + "},")
     out.append("};")
     out.append("")
     # Sum-of-squares forms of the three large indicators (single-precision

@@ -58,9 +58,10 @@ static __constant__ double TENO_LIN6[12] = {
 
 static __constant__ double TENO_DK[3] = {0.5065006634, 0.3699651429, 0.1235341937};
 // Renormalised fallback weights w_k = d_k delta_k / sum_j d_j delta_j (double
-// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index.
+// division), by (delta_0, delta_1, delta_2) = bits 0..2 of the row index;
+// NaN (0/0) when no candidate is kept.
 static __constant__ double TENO_FBW[8][3] = {
-    {0.0, 0.0, 0.0},
+    {__builtin_nan(""), __builtin_nan(""), __builtin_nan("")},
     {0x1.0000000000000p+0, 0.0, 0.0},
     {0.0, 0x1.0000000000000p+0, 0.0},
     {0x1.27e12c8784fa3p-1, 0x1.b03da6f0f60bcp-2, 0.0},
@@ -72,7 +73,7 @@ static __constant__ double TENO_FBW[8][3] = {
 // Fallback as one linear scheme on offsets -2..2, by (delta_0, delta_1,
 // delta_2) = bits 0..2 of the row index.
 static __constant__ double TENO_FBK[8][5] = {
-    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {__builtin_nan(""), __builtin_nan(""), __builtin_nan(""), __builtin_nan(""), __builtin_nan("")},
     {0.0, -0x1.5555555555555p-3, 0x1.aaaaaaaaaaaabp-1, 0x1.5555555555555p-2, 0.0},
     {0.0, 0.0, 0x1.5555555555555p-2, 0x1.aaaaaaaaaaaabp-1, -0x1.5555555555555p-3},
     {0.0, -0x1.8a8190b4b14d9p-4, 0x1.3e9b40ee6d27dp-1, 0x1.16ba1466e82dbp-1, -0x1.202919f5f95d3p-4},

@@ -59,6 +59,9 @@ struct FastK {
     float thr_rej[23];           // thr_rej[n] >= 1 / (10^-n (1 - 2^-16)) - 1
     float eb_lo, eb_hi;          // eps_beta * 2^100 (1 -+ 1e-6) rounded down / up
     float ee_hi;                 // eps_eta * 2^100 rounded up
+    int flat_ok;                 // C_r <= 1 and C_T at m = 0 at most 0.1 (the flat cases'
+                                 // answer, S_p with the smooth exponent, holds)
+    int tiny_ok;                 // flat_ok, and both epsilons at least 2^-136
 };
 
 // Filter switch (teno_set_decision_filter), process-wide.
@@ -100,6 +103,8 @@ inline FastK fastk_make(double cr, double alpha1, double alpha2, double eps_beta
     const double bct = alpha1 - alpha2 * (1.0 - 1.0);
     const double fl = floor(bct);
     F.nexp_smooth = fl < 0.0 ? 0 : (fl > 22.0 ? 22 : (int)fl);
+    F.flat_ok = (cr <= 1.0 && F.nexp_smooth >= 1) ? 1 : 0;
+    F.tiny_ok = (F.flat_ok && eps_beta >= 0x1p-136 && eps_eta >= 0x1p-136) ? 1 : 0;
     const double bmin = alpha1 - alpha2 * (1.0 - 0.0);
     const double flm = floor(bmin);
     F.nexp_min = flm < 0.0 ? 0 : (flm > 22.0 ? 22 : (int)flm);
@@ -336,16 +341,32 @@ __device__ __forceinline__ bool fast_decide(const double (&v)[2 * H], const doub
     const int emax = efield - 1023;
     if (efield == 0) {
         // No shifted value above the subnormal range.  All values bit-identical:
-        // every indicator is exactly 0, chi = 1/4, eta = 1, hence S_p with the
-        // smooth exponent; anything else goes to the exact path.
-        bool all_eq = true;
+        // the exact path's beta_0 and beta_p are 0 and beta_1 = beta_2 (the
+        // rounding of 3 v_0), so chi_p lies in [1/4, 1/2] (or is NaN for
+        // eps = 0, which also keeps S_p), and eta = eps/eps = 1 (m = 0 when
+        // C_r <= 1; NaN for eps = 0, m = 0 too): S_p with the smooth exponent
+        // when C_T <= 0.1 there.  Anything else goes to the exact path.
+        bool all_eq = F.flat_ok != 0;
 #pragma unroll
         for (int j = 0; j < W; j++) all_eq = all_eq && dbits_equal(v[j], v[H - 1]);
         if (!all_eq) return false;
         flag = (uint8_t)(large_code(H) | (((F.nexp_smooth - 7) & 7) << 5));
         return true;
     }
-    if (emax < -100 || emax > 50) return false;
+    if (emax < -100) {
+        // Every shifted value below 2^-100, not all zero: distinct doubles that
+        // close are below 2^-46 in size, so every indicator the exact path
+        // forms, its own rounding included, is below 2^-177 (the largest
+        // form's coefficients sum to 2^23), at most 2^-41 of eps_beta >=
+        // 2^-136.  The x_k = beta_k + eps then agree to 2^-40 and chi_p =
+        // 1/4 (1 +- 2^-35) >= C_T; the eta measure's products (below 2^-194)
+        // vanish next to eps_eta in the rounding, so eta = 1 exactly: S_p
+        // with the smooth exponent.
+        if (!F.tiny_ok) return false;
+        flag = (uint8_t)(large_code(H) | (((F.nexp_smooth - 7) & 7) << 5));
+        return true;
+    }
+    if (emax > 50) return false;
     float f[W];
 #pragma unroll
     for (int j = 0; j < W; j++) f[j] = (j == H - 1) ? 0.0f : d2f_scaled(s[j], emax);

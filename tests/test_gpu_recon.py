@@ -22,8 +22,8 @@ import paper_2109_14340_gb300 as T  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
-def oracle_batch(scheme, V):
-    p = oracle.params(1, [16], [1.0], scheme=scheme)
+def oracle_batch(scheme, V, **kw):
+    p = oracle.params(1, [16], [1.0], scheme=scheme, **kw)
     out = np.empty(len(V))
     fl = np.empty(len(V), np.uint8)
     for i, v in enumerate(V):
@@ -31,10 +31,11 @@ def oracle_batch(scheme, V):
     return out, fl
 
 
-def gpu_batch(scheme, V, fast, with_flags=True):
+def gpu_batch(scheme, V, fast, with_flags=True, **kw):
     """Values and decision bytes (None without a record: the filter may then
-    accept S_p for every C_T the parameters allow without the eta measure)."""
-    p = T.teno_params_init(scheme=scheme)
+    accept S_p for every C_T the parameters allow without the eta measure).
+    kw: teno_params fields."""
+    p = T.teno_params_init(scheme=scheme, **kw)
     T.teno_set_decision_filter(fast)
     try:
         v = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
@@ -44,6 +45,13 @@ def gpu_batch(scheme, V, fast, with_flags=True):
         return out.cpu().numpy(), (fl.cpu().numpy() if with_flags else None)
     finally:
         T.teno_set_decision_filter(True)
+
+
+def differ(a, b):
+    """Mask of values that differ bit for bit, two NaNs counting as equal
+    (their payloads are the host's and the device's; the empty fallback of
+    C_T = 1 is 0/0)."""
+    return (a.view(np.int64) != b.view(np.int64)) & ~(np.isnan(a) & np.isnan(b))
 
 
 def neighbours(x, k=3):
@@ -195,16 +203,39 @@ def noise_stencils(scheme, n=6000, seed=11):
     return np.array(V)
 
 
+def tiny_stencils(scheme, n=3000, seed=13):
+    """Stencils whose differences all lie below 2^-100 (values below 2^-46),
+    bit-identical stencils of every size, and differences in the subnormal
+    range."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    W = scheme
+    V = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            v = g.standard_normal(W) * 10.0 ** g.uniform(-60, -31)
+        elif kind == 1:
+            v0 = g.choice([-1.0, 1.0]) * 10.0 ** g.uniform(-45, -20)
+            v = v0 + g.integers(-3, 4, W) * np.spacing(v0)
+        elif kind == 2:
+            v = np.full(W, g.uniform(-1, 1) * 10.0 ** g.uniform(-300, 300))
+        else:
+            v = g.integers(-3, 4, W) * 5e-324 * float(g.integers(1, 1000))
+        V.append(v)
+    return np.array(V)
+
+
 @pytest.mark.parametrize("scheme", [8, 10, 12])
 def test_reconstruction_matches_oracle(scheme):
-    V = np.concatenate([random_stencils(scheme), adversarial(scheme), noise_stencils(scheme)])
+    V = np.concatenate([random_stencils(scheme), adversarial(scheme), noise_stencils(scheme),
+                        tiny_stencils(scheme)])
     ref, rfl = oracle_batch(scheme, V)
     for fast in (True, False):
         out, fl = gpu_batch(scheme, V, fast)
-        bad = np.nonzero((fl != rfl) | (out.view(np.int64) != ref.view(np.int64)))[0]
+        bad = np.nonzero((fl != rfl) | (differ(out, ref)))[0]
         assert bad.size == 0, (fast, bad[:10], fl[bad[:5]], rfl[bad[:5]])
         out, _ = gpu_batch(scheme, V, fast, with_flags=False)
-        bad = np.nonzero(out.view(np.int64) != ref.view(np.int64))[0]
+        bad = np.nonzero(differ(out, ref))[0]
         assert bad.size == 0, (fast, "no record", bad[:10])
 
 
@@ -221,3 +252,33 @@ def test_adversarial_families_reach_both_sides(scheme):
     # every large stencil S3 .. S_H, and fallbacks with different cut-offs
     assert set(range(3, scheme // 2 + 1)) <= sels
     assert len({d[1] for d in dec if d[0] == 0}) >= 3
+
+
+# (GPU field names, oracle names): C_r > 1 (eta = 1 no longer gives m = 0),
+# C_T = 1 at m = 0 (chi_p = 1/4 rejects S_p), and epsilons below 2^-136
+# (the tiny-difference answer no longer certain).
+PARAM_SETS = [
+    (dict(ct_cr=2.0), dict(cr=2.0)),
+    (dict(ct_alpha1=0.5, ct_alpha2=0.2), dict(alpha1=0.5, alpha2=0.2)),
+    (dict(eps_beta=1e-45, eps_eta=1e-45), dict(eps_beta=1e-45, eps_eta=1e-45)),
+]
+
+
+@pytest.mark.parametrize("scheme", [8, 10])
+@pytest.mark.parametrize("ps", range(len(PARAM_SETS)))
+def test_flat_and_tiny_cases_other_parameters(scheme, ps):
+    """The filter's answers for bit-identical and tiny-difference stencils
+    (S_p with the smooth exponent) rest on C_r <= 1, C_T <= 0.1 at m = 0 and
+    epsilons of at least 2^-136; with parameters that break one of them the
+    results must still be the oracle's, bitwise."""
+    gk, ok = PARAM_SETS[ps]
+    V = np.concatenate([tiny_stencils(scheme, 1200, seed=17), noise_stencils(scheme, 1200, seed=19),
+                        random_stencils(scheme, 1200, seed=23)])
+    ref, rfl = oracle_batch(scheme, V, **ok)
+    for fast in (True, False):
+        out, fl = gpu_batch(scheme, V, fast, **gk)
+        bad = np.nonzero((fl != rfl) | (differ(out, ref)))[0]
+        assert bad.size == 0, (fast, bad[:10], fl[bad[:5]], rfl[bad[:5]])
+        out, _ = gpu_batch(scheme, V, fast, with_flags=False, **gk)
+        bad = np.nonzero(differ(out, ref))[0]
+        assert bad.size == 0, (fast, "no record", bad[:10])

@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(TF, (384 / TF > 1 ? 384 / TF : 1)) batch_face_
         a.K = K;
         a.K.limiter = d.limiter;
         const int64_t f0 = (int64_t)(it - fprefix[p]) * TF;
-        if (d.scheme == 10) face_block<1, 5, 0, 1, TF>(a, f0, 0, 0, 0, sm);
-        else face_block<1, 4, 0, 1, TF>(a, f0, 0, 0, 0, sm);
+        if (d.scheme == 10) face_block<1, 5, 0, 1, TF, kSweepPlain>(a, f0, 0, 0, 0, sm);
+        else face_block<1, 4, 0, 1, TF, kSweepPlain>(a, f0, 0, 0, 0, sm);
         __syncthreads();
     }
 }

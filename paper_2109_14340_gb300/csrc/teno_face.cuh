@@ -169,12 +169,17 @@ constexpr size_t face_smem_bytes()
            (size_t)(TP * TF) * 2 * (ND + 2);
 }
 
+// Sweep modes, a compile-time choice so that each kernel holds only its own
+// code: a plain sweep, one that writes the decision record (flags, argmax,
+// limrec), and one that applies recorded decisions (frozen, frozen_argmax).
+enum { kSweepPlain = 0, kSweepRecord = 1, kSweepFrozen = 2 };
+
 // One tile: faces f0 .. f0+TF-1 along D of the TP pencils starting at x0
 // (at y, z for the axes not swept); for D = 0 the pencils run along y instead,
 // starting at y (x0 unused).  Every thread of the block calls it; it
 // synchronises once after staging and returns with no barrier pending, so a
 // persistent caller must synchronise before reusing the shared tile.
-template <int ND, int H, int D, int TP, int TF>
+template <int ND, int H, int D, int TP, int TF, int MODE>
 __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_t x0, int64_t y,
                                            int64_t z, double *sm)
 {
@@ -286,7 +291,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
         else flin = pstart + p + n0 * (y + n1 * f);
         if (!TENO_IN(a.st, flin, a.nfaces)) flin = 0;        // debug build: counted, redirected
         // Splitting speeds over the stencil (first maximum), or at recorded cells.
-        if (a.frozen_argmax) {
+        if constexpr (MODE == kSweepFrozen) {
             unsigned w = a.frozen_argmax[flin];
             if (!TENO_IN(a.st, (int)(w & 15), W) || !TENO_IN(a.st, (int)((w >> 4) & 15), W) ||
                 !TENO_IN(a.st, (int)((w >> 8) & 15), W) || !TENO_IN(a.st, (int)(w >> 12), W))
@@ -306,7 +311,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
                 if (j == 0 || speed_gt(ep, ap)) { ap = ep; jp = j; }
                 if (j == 0 || speed_gt(er, ar)) { ar = er; jr_ = j; }
             }
-            if (a.argmax) a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
+            if constexpr (MODE == kSweepRecord)
+                a.argmax[flin] = (uint16_t)(jm | (j0 << 4) | (jp << 8) | (jr_ << 12));
         }
     }
 
@@ -363,14 +369,15 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             double val = 0.0;
             uint8_t fl = 0;
             bool done = true;
-            if (a.frozen) {
+            if constexpr (MODE == kSweepFrozen) {
                 fl = a.frozen[(flin * nc + k) * 2 + s];
                 val = frozen_recon<H>(v, fl);
             } else {
                 double sh[W];
 #pragma unroll
                 for (int kk = 0; kk < W; kk++) sh[kk] = v[kk] - v[H - 1];
-                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl, a.need_ct != 0);
+                const bool dec = a.fast && fast_decide<H>(v, sh, a.FK, fl,
+                                                          MODE == kSweepRecord && a.need_ct != 0);
                 // the largest stencil accepted (S6 as bits 0-4 zero).  Kept
                 // inline: the same test through a helper function made the 8-
                 // and 10-point sweeps 4-14 % slower (same registers, other code).
@@ -397,11 +404,11 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             }
             if (done) {
                 Qres[threadIdx.x * (2 * nc) + 2 * k + s] = val;
-                if (a.flags) a.flags[(flin * nc + k) * 2 + s] = fl;
+                if constexpr (MODE == kSweepRecord) a.flags[(flin * nc + k) * 2 + s] = fl;
             }
         }
     }
-    if (!a.frozen) {
+    if constexpr (MODE != kSweepFrozen) {
         __syncthreads();
         const int ne = min(qcount[0], QE), nd = min(qcount[1], CAP - QE);
         if (a.exact_count && threadIdx.x == 0 && qcount[0] > 0)
@@ -428,11 +435,12 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
             if (TENO_IN(a.st, slot, TP * TF * 2 * nc)) Qres[slot] = decided_value<H>(v, Qfl[slot]);
         }
         __syncthreads();
-        if (active && pending) {
+        if constexpr (MODE == kSweepRecord) {
+            if (active && pending) {
 #pragma unroll
-            for (int q = 0; q < 2 * nc; q++) {
-                if (pending & (1u << q)) {
-                    if (a.flags) a.flags[(flin * nc + (q >> 1)) * 2 + (q & 1)] = Qfl[threadIdx.x * (2 * nc) + q];
+                for (int q = 0; q < 2 * nc; q++) {
+                    if (pending & (1u << q))
+                        a.flags[(flin * nc + (q >> 1)) * 2 + (q & 1)] = Qfl[threadIdx.x * (2 * nc) + q];
                 }
             }
         }
@@ -520,8 +528,8 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #pragma unroll
             for (int c = 0; c < nc; c++) Fo[c] = FL[c] + thp * dF[c];
         }
-        if (a.limrec) a.limrec[flin] = thp < 1.0 ? 1 : 0;
-    } else if (a.limrec) {
+        if constexpr (MODE == kSweepRecord) a.limrec[flin] = thp < 1.0 ? 1 : 0;
+    } else if constexpr (MODE == kSweepRecord) {
         a.limrec[flin] = 0;
     }
 
@@ -530,7 +538,7 @@ __device__ __forceinline__ void face_block(const FaceArgs &a, int64_t f0, int64_
 #undef SQ
 }
 
-template <int ND, int H, int D, int TP, int TF>
+template <int ND, int H, int D, int TP, int TF, int MODE>
 __global__ void __launch_bounds__(TP * TF, FaceTile<ND, H>::MINB) face_kernel(FaceArgs a)
 {
     extern __shared__ double sm[];
@@ -538,31 +546,45 @@ __global__ void __launch_bounds__(TP * TF, FaceTile<ND, H>::MINB) face_kernel(Fa
     if (D == 0) { f0 = (int64_t)blockIdx.x * TF; y = (int64_t)blockIdx.y * TP; z = blockIdx.z; }
     else if (D == 1) { x0 = (int64_t)blockIdx.x * TP; f0 = (int64_t)blockIdx.y * TF; z = blockIdx.z; }
     else { f0 = (int64_t)blockIdx.x * TF; x0 = (int64_t)blockIdx.y * TP; y = blockIdx.z; }
-    face_block<ND, H, D, TP, TF>(a, f0, x0, y, z, sm);
+    face_block<ND, H, D, TP, TF, MODE>(a, f0, x0, y, z, sm);
 }
 
-// Host-side launch of one direction's sweep.
-template <int ND, int H, int D>
-cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
+template <int ND, int H, int D, int MODE>
+cudaError_t launch_face_mode(const FaceArgs &a, dim3 grid, cudaStream_t s)
 {
     constexpr int TP = FaceTile<ND, H>::TP;
     constexpr int TF = FaceTile<ND, H>::TF;
     constexpr size_t smem = face_smem_bytes<ND, H, TP, TF>();
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(face_kernel<ND, H, D, TP, TF>,
+        cudaError_t e = cudaFuncSetAttribute(face_kernel<ND, H, D, TP, TF, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    face_kernel<ND, H, D, TP, TF, MODE><<<grid, TP * TF, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Host-side launch of one direction's sweep, in the mode its arguments ask
+// for (a decision record to write, recorded decisions to apply, or neither).
+template <int ND, int H, int D>
+cudaError_t launch_face(const FaceArgs &a, cudaStream_t s)
+{
+    constexpr int TP = FaceTile<ND, H>::TP;
+    constexpr int TF = FaceTile<ND, H>::TF;
+    if ((a.flags && a.frozen) || (a.flags && (!a.argmax || !a.limrec)) ||
+        (a.frozen && !a.frozen_argmax))
+        return cudaErrorInvalidValue;
     dim3 grid;
     const int64_t nf = a.n[D] + 1 - a.skip_last;    // faces computed along D
     if (D == 0) grid = dim3((unsigned)((nf + TF - 1) / TF), (unsigned)((a.n[1] + TP - 1) / TP), (unsigned)a.n[2]);
     else if (D == 1) grid = dim3((unsigned)((a.n[0] + TP - 1) / TP), (unsigned)((nf + TF - 1) / TF), (unsigned)a.n[2]);
     else   // z tiles fastest: consecutive blocks share their halo planes through L2
         grid = dim3((unsigned)((nf + TF - 1) / TF), (unsigned)((a.n[0] + TP - 1) / TP), (unsigned)a.n[1]);
-    face_kernel<ND, H, D, TP, TF><<<grid, TP * TF, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.flags) return launch_face_mode<ND, H, D, kSweepRecord>(a, grid, s);
+    if (a.frozen) return launch_face_mode<ND, H, D, kSweepFrozen>(a, grid, s);
+    return launch_face_mode<ND, H, D, kSweepPlain>(a, grid, s);
 }
 
 }  // namespace teno

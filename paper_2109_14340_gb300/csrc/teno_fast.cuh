@@ -39,7 +39,10 @@
 // large as the differences.  When the values' exponent exceeds the common
 // scale by 30 or more, the filter takes the small indicators' inputs with
 // the exact path's FP64 operations (bitwise its values) and bounds only
-// their conversion to FP32.
+// their conversion to FP32.  Bit-identical stencils, and stencils whose
+// differences all lie below 2^-100, are answered outright (S_p with the
+// smooth exponent) where the parameters make that answer certain: C_r <= 1,
+// C_T <= 0.1 at m = 0 and, for the second kind, epsilons of at least 2^-136.
 #pragma once
 
 #include <cmath>

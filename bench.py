@@ -55,6 +55,8 @@ def parse_args():
                     help="skip the TENO12-AA line (same workload, twelve-point scheme)")
     ap.add_argument("--no-teno8", action="store_true",
                     help="skip the TENO8-AA line (same workload, eight-point scheme)")
+    ap.add_argument("--no-2d", action="store_true",
+                    help="skip the 2D 1024^2 four-quadrant line")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload and print its record (profiling)")
     ap.add_argument("--batched-no-reference", action="store_true",
@@ -717,6 +719,63 @@ def run_scheme_leg(args, dev, stream, scheme, n=256, steps=3):
     }
 
 
+def run_2d_leg(args, dev, stream, scheme=10, n=1024, warm=45, steps=20):
+    """The 2D four-quadrant Riemann problem at 1024^2 (TENO10-AA,
+    transmissive sides, CFL 0.4), timed after `warm` steps, when rounding
+    noise has spread over its constant states (the decisions there follow
+    the noise, which the decision filter must still certify): rate, the
+    share of reconstructions that reached the exact FP64 path, and the face
+    kernel's FP64 roofline fraction."""
+    import torch
+
+    import paper_2109_14340_gb300 as T
+    import workloads
+    case = workloads.quadrants_2d(n, scheme=scheme)
+    p = T.teno_params_init(ndim=2, n=case["n"], dx=case["dx"], scheme=scheme,
+                           bc_lo=case["bc_lo"], bc_hi=case["bc_hi"])
+    solver = T.Solver(p, dev)
+    U = torch.from_numpy(case["U"]).to(dev)
+
+    def step():
+        solver.cfl_dt(U)
+        solver.step(U)
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize(dev)
+    _, flags = solver.rhs(U, flags=True)
+    fl_np = flags.cpu().numpy()[:T.record_layout(p)[1]]      # decision bytes
+    fpf, hist = flops_per_face_from_flags(fl_np, 2, scheme // 2)
+    del flags, fl_np
+    clocks = ClockSampler(dev.index)
+    T.teno_profile_enable(True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    face_ms, face_launches, face_faces, face_exact = T.teno_profile_read()
+    T.teno_profile_enable(False)
+    clk = clocks.stop()
+    avg_launch_s = face_ms * 1e-3 / max(face_launches, 1)
+    faces_per_launch = face_faces / max(face_launches, 1)
+    exact_frac = face_exact / max(face_faces * 2 * 4, 1)
+    roof = fp64_roofline(hist, exact_frac, 2, scheme // 2, faces_per_launch, avg_launch_s, fpf)
+    roof.update({"exact_path_fraction": exact_frac, "avg_launch_ms": avg_launch_s * 1e3,
+                 "traffic": None, "face_kernel_share": face_ms / ms if ms > 0 else None,
+                 "selection_mix": selection_mix(hist, scheme)})
+    return {
+        "workload": "2D Euler %dx%d four-quadrant Riemann problem + entropy wave, TENO%d-AA, "
+                    "LLF, transmissive sides, CFL 0.4, timed after %d steps" % (n, n, scheme, warm),
+        "steps": steps, "ms_per_step": ms / steps, "value": n * n / (ms / steps * 1e-3),
+        "unit": UNIT, "nonphysical": solver.status(), "clocks": clk, "roofline": roof,
+    }
+
+
 def measured_hbm_peak():
     """HBM copy bandwidth from MEASURED_PEAKS.json (measured on this machine's
     GB300s), else the profiling recipe's fallback."""
@@ -909,6 +968,9 @@ def run_ours(args, rank, world, local_rank):
     teno8 = None
     if not args.no_teno8 and scheme != 8:
         teno8 = run_scheme_leg(args, dev, stream, 8, n=n)
+    quad2d = None
+    if not args.no_2d:
+        quad2d = run_2d_leg(args, dev, stream)
 
     if rank != 0:
         if dist is not None:
@@ -950,6 +1012,7 @@ def run_ours(args, rank, world, local_rank):
         "noh": noh,
         "teno12": teno12,
         "teno8": teno8,
+        "quadrants_2d": quad2d,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

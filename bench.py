@@ -57,6 +57,8 @@ def parse_args():
                     help="skip the TENO8-AA line (same workload, eight-point scheme)")
     ap.add_argument("--no-2d", action="store_true",
                     help="skip the 2D 1024^2 four-quadrant line")
+    ap.add_argument("--2d-only", dest="quadrants_2d_only", action="store_true",
+                    help="run only the 2D four-quadrant line and print its record (profiling)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload and print its record (profiling)")
     ap.add_argument("--batched-no-reference", action="store_true",
@@ -1035,13 +1037,14 @@ def main():
         torch.cuda.set_device(dev)
         print(json.dumps(run_batched(args, dev, torch.cuda.current_stream(dev))), flush=True)
         return
-    if args.adjoint_only:
+    if args.adjoint_only or args.quadrants_2d_only:
         import torch
         from paper_2109_14340_gb300 import _build
         _build.build()
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
-        print(json.dumps(run_adjoint(args, dev, torch.cuda.current_stream(dev))), flush=True)
+        run = run_adjoint if args.adjoint_only else run_2d_leg
+        print(json.dumps(run(args, dev, torch.cuda.current_stream(dev))), flush=True)
         return
     run_ours(args, rank, world, local_rank)
 

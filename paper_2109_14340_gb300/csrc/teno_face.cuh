@@ -153,7 +153,10 @@ struct FaceTile {
 #else
     static constexpr int TP = ND == 1 ? 1 : 4;
     static constexpr int TF = ND == 1 ? 128 : 32;
-    static constexpr int QCAP = 2;
+    // 2D ten-point: four queue entries per thread still fit three blocks per
+    // SM (73 KB each); noise plateaus hold about eight decided, non-S_p
+    // reconstructions per thread, which otherwise diverge when done in place
+    static constexpr int QCAP = (ND == 2 && H == 5) ? 4 : 2;
     static constexpr int MINB = ND >= 2 ? (H == 4 ? 4 : 3) : 1;
 #endif
 };

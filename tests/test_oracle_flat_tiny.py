@@ -65,3 +65,24 @@ def test_flat_and_tiny_stencils_select_smooth_sp(scheme, eps):
             if fl != want:
                 bad.append((v, fl))
         assert not bad, (name, len(bad), bad[:3], want)
+
+
+def test_empty_fallback_is_nan():
+    """Reading of Eq. renormalize when every small-stencil cut-off fails,
+    possible only for C_T = 1 ([beta] = 0): the weights are 0/0, so the
+    oracle's value is NaN exactly for the fallbacks that keep no stencil,
+    and a number for every other outcome."""
+    po = oracle.params(1, [16], [1.0], scheme=10, alpha1=0.5, alpha2=0.2)
+    g = np.random.Generator(np.random.PCG64(41))
+    empty = kept = 0
+    for i in range(3000):
+        v = g.standard_normal(10) * 10.0 ** g.uniform(-3, 3) + g.uniform(-5, 5)
+        val, fl = oracle.recon(po, v)
+        sel, mask = fl & 3, (fl >> 2) & 7
+        if sel == 0 and mask == 0:
+            assert np.isnan(val)
+            empty += 1
+        else:
+            assert np.isfinite(val)
+            kept += 1
+    assert empty > 1000 and kept >= 10
